@@ -1,0 +1,416 @@
+#!/usr/bin/env python3
+"""Benchmark of the SCF + MEX expansion force calculation on GB300.
+
+One step = one full SCF force calculation (coefficient pass + field pass,
+(n_max, l_max) = (10, 6)) and one full MEX force calculation (radial sort,
+inner/outer scans, field; l_max = 6) on the same N = 2^20 particles of a
+Hernquist model stretched to axis ratios 1 : 0.8 : 0.6, in the mixed precision
+path (FP32 arithmetic, FP64 coefficient reduction and scan carries).  The
+metric is particle-forces per second: 2N per step (N by each method).
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle (the
+FP64 reference implementation written from the paper) on a bounded sample of
+the same workload instead.  Multi-GPU (torchrun): independent replicas, one
+per GPU (the methods are not sharded), weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle forces/s at N=2^20 (SCF n10 l6; MEX l6), mixed vs FP64, same GB300"
+UNIT = "particle-forces/s"
+N_DEFAULT = 1 << 20
+N_MAX, L_MAX = 10, 6
+FP32_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (max SM clock)"
+
+
+def workload_name(n):
+    return f"hernquist-1:0.8:0.6 N={n} SCF(n_max=10,l_max=6)+MEX(l_max=6)"
+
+
+# --- algorithmic work per particle (kept in sync with the design doc) ------------
+def scf_coeff_flops(n, l):
+    # contraction 2(n+1)(l+1)^2 + Gegenbauer 3(n+1)(l+1) + angular 4(l+1)^2 + 30
+    return 2 * (n + 1) * (l + 1) ** 2 + 3 * (n + 1) * (l + 1) + 4 * (l + 1) ** 2 + 30
+
+
+def scf_field_flops(n, l):
+    # contraction 4(n+1)(l+1)^2 + basis 6(n+1)(l+1) + angular+gradient 10(l+1)^2
+    # + radial prefactors 8(l+1) + 80
+    return 4 * (n + 1) * (l + 1) ** 2 + 6 * (n + 1) * (l + 1) + 10 * (l + 1) ** 2 \
+        + 8 * (l + 1) + 80
+
+
+def mex_bytes(fp64=False):
+    # keys 16R+12W, 4 sort passes (8R+8W), tie pass 4R, gather 4R+16R+16W,
+    # pass2 16R+4R+16W  (per particle, FP32 particles)
+    b = 16 + 12 + 4 * 16 + 4 + (4 + 16 + 16) + (16 + 4 + 16)
+    return b + (3 * 16 if fp64 else 0)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# --- clocks sampling ---------------------------------------------------------
+class Clocks:
+    def __init__(self, index=0):
+        self.proc = None
+        self.path = None
+        self.index = index
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# --- GPU arm -------------------------------------------------------------------
+def run_etics(args, rank, world):
+    import torch
+    from paper_1406_4254_gb300 import etics, inputs
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    n = args.n
+    pm = inputs.hernquist(n, seed=args.seed + rank, axes=(1.0, 0.8, 0.6))
+    x = torch.tensor(pm, dtype=torch.float32, device=dev)
+    x64 = torch.tensor(pm, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    coeffs = torch.empty((N_MAX + 1, (L_MAX + 1) ** 2), dtype=torch.float64, device=dev)
+    out_scf = torch.empty_like(x)
+    out_mex = torch.empty_like(x)
+    ws_scf = etics.workspace(n, N_MAX, L_MAX, etics.SCF, etics.MIXED, dev)
+    ws_mex = etics.workspace(n, 0, L_MAX, etics.MEX, etics.MIXED, dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 126 MB L2
+
+    # stage events: [scf: 0 start, 1 coeff kernel end, 2 end][field 0,1][mex 0..5]
+    ev = {k: [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+          for k in ("coef", "field", "mex")}
+
+    def step(timed_stages=False):
+        if timed_stages:
+            etics.set_stage_events(ev["coef"][:3])
+        etics.scf_coeffs(x, N_MAX, L_MAX, out=coeffs, ws=ws_scf)
+        if timed_stages:
+            etics.set_stage_events(ev["field"][:2])
+        etics.scf_field(x, coeffs, N_MAX, L_MAX, out=out_scf)
+        if timed_stages:
+            etics.set_stage_events(ev["mex"])
+        etics.mex_field(x, L_MAX, out=out_mex, ws=ws_mex)
+        if timed_stages:
+            etics.set_stage_events(None)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    etics.check_error()
+
+    clocks = Clocks(local)
+    times, stage = [], {k: [] for k in ("coef_kernel", "finalize", "field_kernel", "mex_keys",
+                                         "mex_sort", "mex_tile_sums", "mex_carry", "mex_pass2",
+                                         "scf", "mex")}
+    l0 = etics.launch_count()
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for _ in range(args.steps):
+        flush.fill_(1)                    # L2 flushed between timed steps
+        t_start.record(stream)
+        step(timed_stages=True)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        times.append(t_start.elapsed_time(t_end))
+        e = ev
+        stage["coef_kernel"].append(e["coef"][0].elapsed_time(e["coef"][1]))
+        stage["finalize"].append(e["coef"][1].elapsed_time(e["coef"][2]))
+        stage["field_kernel"].append(e["field"][0].elapsed_time(e["field"][1]))
+        stage["scf"].append(e["coef"][0].elapsed_time(e["field"][1]))
+        stage["mex_keys"].append(e["mex"][0].elapsed_time(e["mex"][1]))
+        stage["mex_sort"].append(e["mex"][1].elapsed_time(e["mex"][2]))
+        stage["mex_tile_sums"].append(e["mex"][2].elapsed_time(e["mex"][3]))
+        stage["mex_carry"].append(e["mex"][3].elapsed_time(e["mex"][4]))
+        stage["mex_pass2"].append(e["mex"][4].elapsed_time(e["mex"][5]))
+        stage["mex"].append(e["mex"][0].elapsed_time(e["mex"][5]))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = etics.launch_count() - l0
+    etics.check_error()
+    ms = statistics.mean(times)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = 2 * n * world / (ms * 1e-3)
+
+    # ---- e2e: host (pinned) buffers through the public API ------------------
+    host_in = torch.tensor(pm, dtype=torch.float32).pin_memory()
+    host_scf = torch.empty((n, 4), dtype=torch.float32).pin_memory()
+    host_mex = torch.empty((n, 4), dtype=torch.float32).pin_memory()
+    dx = torch.empty_like(x)
+
+    def e2e_step():
+        dx.copy_(host_in, non_blocking=True)
+        etics.scf_coeffs(dx, N_MAX, L_MAX, out=coeffs, ws=ws_scf)
+        etics.scf_field(dx, coeffs, N_MAX, L_MAX, out=out_scf)
+        etics.mex_field(dx, L_MAX, out=out_mex, ws=ws_mex)
+        host_scf.copy_(out_scf, non_blocking=True)
+        host_mex.copy_(out_mex, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_t = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.fill_(1)
+        t_start.record(stream)
+        e2e_step()
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        e2e_t.append(t_start.elapsed_time(t_end))
+    e2e_ms = statistics.mean(e2e_t)
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    # ---- FP64 GPU path (same particles), a few steps -------------------------
+    ws64s = etics.workspace(n, N_MAX, L_MAX, etics.SCF, etics.FP64, dev)
+    ws64m = etics.workspace(n, 0, L_MAX, etics.MEX, etics.FP64, dev)
+    o64 = torch.empty_like(x64)
+    c64 = torch.empty_like(coeffs)
+    def step64():
+        etics.scf_coeffs(x64, N_MAX, L_MAX, out=c64, ws=ws64s)
+        etics.scf_field(x64, c64, N_MAX, L_MAX, out=o64)
+        t_mid.record(stream)
+        etics.mex_field(x64, L_MAX, out=o64, ws=ws64m)
+    t_mid = torch.cuda.Event(enable_timing=True)
+    step64()
+    torch.cuda.synchronize()
+    f64_scf, f64_mex = [], []
+    for _ in range(3):
+        flush.fill_(1)
+        t_start.record(stream)
+        step64()
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        f64_scf.append(t_start.elapsed_time(t_mid))
+        f64_mex.append(t_mid.elapsed_time(t_end))
+    etics.check_error()
+
+    result = None
+    if rank == 0:
+        result = {"ms": ms, "value": value, "stage": {k: statistics.mean(v) for k, v in stage.items()},
+                  "launches": launches, "clocks": clk, "e2e_ms": e2e_ms,
+                  "f64": (statistics.mean(f64_scf), statistics.mean(f64_mex)),
+                  "out_scf": out_scf, "out_mex": out_mex, "pm": pm}
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return result
+
+
+def accuracy(pm, out_scf, out_mex, sample=4096):
+    """eps~ of eq. 18 of the mixed path against the FP64 oracle at the same
+    (FP32-rounded) positions: SCF coefficients from all particles and field on
+    a sample; MEX on all particles."""
+    import oracle
+    ref = pm.astype(np.float32).astype(np.float64)
+    c = oracle.scf_coeffs(ref[:, :3], ref[:, 3], N_MAX, L_MAX)
+    idx = np.random.default_rng(0).choice(len(pm), min(sample, len(pm)), replace=False)
+    a_ref, _ = oracle.scf_field(ref[idx, :3], N_MAX, L_MAX, c)
+    a = out_scf.cpu().numpy()[idx, :3]
+    es = np.linalg.norm(a - a_ref, axis=1) / np.linalg.norm(a_ref, axis=1)
+    a_ref, _, _ = oracle.mex_field(ref[:, :3], ref[:, 3], L_MAX)
+    a = out_mex.cpu().numpy()[:, :3]
+    em = np.linalg.norm(a - a_ref, axis=1) / np.linalg.norm(a_ref, axis=1)
+
+    def st(e):
+        return {"median": float(np.median(e)), "p99": float(np.quantile(e, 0.99)),
+                "max": float(e.max())}
+    return {"scf": st(es) | {"sample": len(idx)}, "mex": st(em) | {"sample": len(pm)}}
+
+
+def oracle_step_time(pm_sample):
+    """Wall time of one oracle SCF (coeffs + field) and one MEX calculation."""
+    import oracle
+    x, m = pm_sample[:, :3], pm_sample[:, 3]
+    t0 = time.perf_counter()
+    c = oracle.scf_coeffs(x, m, N_MAX, L_MAX)
+    oracle.scf_field(x, N_MAX, L_MAX, c)
+    t1 = time.perf_counter()
+    oracle.mex_field(x, m, L_MAX)
+    t2 = time.perf_counter()
+    return t1 - t0, t2 - t1
+
+
+def cpu_baseline(n_sample, repeats, seed=0):
+    import oracle
+    from paper_1406_4254_gb300 import inputs
+    pm = inputs.hernquist(n_sample, seed=seed, axes=(1.0, 0.8, 0.6))
+    ts = [oracle_step_time(pm) for _ in range(repeats)]
+    t = statistics.mean(a + b for a, b in ts)
+    return {"value": 2 * n_sample / t, "unit": UNIT, "cores": oracle.default_threads(),
+            "kind": "oracle",
+            "sample": (f"{n_sample} particles of the same model, {repeats} steps; SCF field pass "
+                       f"threaded over particles, SCF coefficient and MEX passes serial")}
+
+
+def emit(obj):
+    print(json.dumps(obj), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["etics", "reference"], default="etics")
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=65536)
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    cfg = {"workload": workload_name(args.n), "N": args.n, "n_max": N_MAX, "l_max": L_MAX,
+           "methods": "SCF+MEX per step", "precision": "mixed (FP32 arithmetic, FP64 reductions)",
+           "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) between timed steps"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        n_s = 16384
+        from paper_1406_4254_gb300 import inputs
+        pm = inputs.hernquist(n_s, seed=0, axes=(1.0, 0.8, 0.6))
+        for _ in range(args.warmup):
+            oracle_step_time(pm)
+        times = [sum(oracle_step_time(pm)) for _ in range(args.steps)]
+        import oracle
+        t = statistics.mean(times)
+        v = 2 * n_s / t
+        emit({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+              "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+              "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+              "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+              "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.default_threads(),
+                               "kind": "oracle",
+                               "sample": f"{n_s} particles of the workload per step"},
+              "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                      "d2h_bytes_per_step": 0}})
+        return
+
+    res = run_etics(args, rank, world)
+    if rank != 0:
+        return
+    peaks, src = load_peaks()
+    n = args.n
+    st = res["stage"]
+    # dominant kernel by time share
+    kern = {"scf_coeff_kernel": st["coef_kernel"], "scf_field_kernel": st["field_kernel"],
+            "mex_sort(5 kernels)": st["mex_sort"], "mex_pass2_kernel": st["mex_pass2"]}
+    dom = max(kern, key=kern.get)
+    sm_max = 2070.0
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12       # TFLOP/s
+    if dom in ("scf_coeff_kernel", "scf_field_kernel"):
+        fl = scf_coeff_flops(N_MAX, L_MAX) if dom == "scf_coeff_kernel" else \
+            scf_field_flops(N_MAX, L_MAX)
+        ach = fl * n / (kern[dom] * 1e-3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": ach / fp32_peak, "traffic": None,
+                "peak_note": FP32_PEAK_NOTE + " (derived, not in MEASURED_PEAKS.json)",
+                "work_per_particle_flop": fl}
+    else:
+        ach = mex_bytes() * n / (kern[dom] * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                "peak_note": f"hbm_gbs of MEASURED_PEAKS.json ({src})"}
+    other = {}
+    for k in ("scf_coeff_kernel", "scf_field_kernel"):
+        fl = scf_coeff_flops(N_MAX, L_MAX) if k == "scf_coeff_kernel" else \
+            scf_field_flops(N_MAX, L_MAX)
+        a = fl * n / (kern[k] * 1e-3) / 1e12
+        other[k] = {"ms": kern[k], "TFLOP/s": a, "frac_fp32": a / fp32_peak}
+    out = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic", "config": cfg, "roofline": roof,
+           "e2e": {"value": 2 * n * world / (res["e2e_ms"] * 1e-3), "unit": UNIT,
+                   "h2d_bytes_per_step": n * 16, "d2h_bytes_per_step": 2 * n * 16},
+           "gpu_launches": res["launches"], "clocks": res["clocks"],
+           "stages_ms": {k: round(v, 5) for k, v in st.items()},
+           "kernels": other,
+           "fp64_path": {"scf_ms": res["f64"][0], "mex_ms": res["f64"][1],
+                         "value": 2 * n / ((res["f64"][0] + res["f64"][1]) * 1e-3),
+                         "scf_particle_forces_per_s": n / (res["f64"][0] * 1e-3),
+                         "mex_particle_forces_per_s": n / (res["f64"][1] * 1e-3)},
+           "mixed_per_method": {"scf_particle_forces_per_s": n / (st["scf"] * 1e-3),
+                                "mex_particle_forces_per_s": n / (st["mex"] * 1e-3)}}
+    if not args.no_accuracy:
+        out["accuracy_eps_vs_oracle"] = accuracy(res["pm"], res["out_scf"], res["out_mex"])
+    if not args.no_cpu_baseline and world >= 1:
+        out["cpu_baseline"] = cpu_baseline(args.cpu_sample, 3)
+    emit(out)
+
+
+if __name__ == "__main__":
+    main()

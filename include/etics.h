@@ -1,0 +1,140 @@
+/*
+ * etics.h -- C ABI of the GB300 (sm_103a) SCF and MEX expansion force library.
+ *
+ * Method: Meiron, Li, Holley-Bockelmann & Spurzem, "Expansion Techniques for
+ * Collisionless Stellar Dynamical Simulations" (the ETICS code).  The problem
+ * (Sec. 2.1, eqs. 1-3) is the Poisson equation of N point masses with G = 1;
+ * the library returns the acceleration a = -grad(Phi) and the potential Phi at
+ * every particle by one of two expansions:
+ *   SCF (Sec. 2.3 eq. 16, Sec. 2.4, Sec. 3.3): coefficients of the
+ *       Hernquist-Ostriker basis, then a field pass over the coefficients;
+ *   MEX (Sec. 2.3 eqs. 13-15, Sec. 2.2, Sec. 3.2): radial sort, then inner and
+ *       outer cumulative multipole sums along radius.
+ *
+ * Conventions shared by every entry point
+ *   - Expansion centre at the origin, Hernquist scale length a = 1 (Sec. 5.1).
+ *   - precision = ETICS_MIXED: particle arrays are float4 (16 B per particle),
+ *     basis recursions and field sums in FP32, coefficient reductions and the
+ *     MEX cross-tile carries in FP64.  precision = ETICS_FP64: arrays are 4
+ *     doubles per particle (32 B) and everything is FP64.
+ *   - posm  [N] = (x, y, z, m);  vel [N] = (vx, vy, vz, unused);
+ *     accpot[N] = (ax, ay, az, Phi), in the caller's particle order.
+ *   - Real orthonormal spherical harmonics without the Condon-Shortley phase:
+ *     Y_l0 = N_l0 P_l^0(cos t), Y_lm = sqrt2 N_lm P_l^m cos(m phi),
+ *     Y_l-m = sqrt2 N_lm P_l^m sin(m phi) (m > 0), so Y_11 = +sqrt(3/4pi) x/r.
+ *     SCF coefficients are doubles c[n*(l_max+1)^2 + l*l + l + m] with
+ *     Phi(x) = sum c * phi_nl(r) Y_lm, phi_nl = -r^l (1+r)^-(2l+1) C_n^(2l+3/2)(xi),
+ *     xi = (r-1)/(r+1).  A_000 = c[0]/sqrt(4 pi) equals the mass of a
+ *     Hernquist system.
+ *   - All pointers except those named "host" are DEVICE pointers owned by the
+ *     caller; the library never frees them and allocates no device memory.
+ *     posm/vel/accpot must be 16-byte aligned; ws 256-byte aligned.
+ *   - stream is a cudaStream_t (NULL = legacy default stream).  Every call is
+ *     asynchronous on it and returns a status: argument errors are reported
+ *     synchronously (nothing is launched); data errors (non-finite input,
+ *     FP32 overflow, a lookback wait that timed out) set a device error word
+ *     that etics_get_error() reads.
+ *   - Limits: 0 <= n_max <= ETICS_NMAX_LIMIT, 0 <= l_max <= ETICS_LMAX_LIMIT
+ *     (SCF); 0 <= l_max <= ETICS_MEX_LMAX_LIMIT (MEX); N < 2^31.
+ *   - Results are deterministic: the same inputs on the same device give
+ *     bitwise identical outputs.
+ */
+#ifndef ETICS_H
+#define ETICS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ETICS_VERSION 100
+
+enum etics_status {
+    ETICS_OK = 0,
+    ETICS_ERR_ARG = -1,         /* invalid argument (null/misaligned pointer, bad size)   */
+    ETICS_ERR_CUDA = -2,        /* a CUDA runtime call failed                             */
+    ETICS_ERR_WORKSPACE = -3,   /* ws_bytes smaller than etics_workspace_bytes()          */
+    ETICS_ERR_NONFINITE = -4,   /* device: NaN/Inf input or FP32 overflow in a sum        */
+    ETICS_ERR_TIMEOUT = -5,     /* device: a bounded inter-block wait gave up             */
+    ETICS_ERR_UNSUPPORTED = -6  /* parameters beyond the compiled limits                  */
+};
+
+enum etics_precision { ETICS_FP64 = 0, ETICS_MIXED = 1 };
+enum etics_method { ETICS_SCF = 0, ETICS_MEX = 1 };
+enum etics_out { ETICS_OUT_ACC = 1, ETICS_OUT_POT = 2 };   /* force/potential/both */
+
+#define ETICS_NMAX_LIMIT 16
+#define ETICS_LMAX_LIMIT 14
+#define ETICS_MEX_LMAX_LIMIT 6
+
+/* Bytes of device workspace a call of `method` (ETICS_SCF: etics_scf_coeffs
+ * and etics_leapfrog_step with SCF; ETICS_MEX: etics_mex_field,
+ * etics_radial_sort and etics_leapfrog_step with MEX) needs on the current
+ * device.  Returns 0 for invalid arguments. */
+size_t etics_workspace_bytes(int64_t N, int n_max, int l_max, int method, int precision);
+
+/* SCF coefficient pass (Sec. 3.3, first part; eq. 16):
+ *   c[n][l,m] = (1/J_nl) sum_k m_k phi_nl(r_k) Y_lm(x_k),
+ *   J_nl = int rho_nl phi_nl r^2 dr.
+ * coeffs: device double[(n_max+1)*(l_max+1)^2], overwritten.  ws: device
+ * workspace of at least etics_workspace_bytes(N, n_max, l_max, ETICS_SCF, p).
+ * N = 0 writes zeros. */
+int etics_scf_coeffs(const void *posm, int64_t N, int n_max, int l_max, int precision,
+                     double *coeffs, void *ws, size_t ws_bytes, void *stream);
+
+/* SCF field pass (Sec. 3.3, second part): Phi = sum c phi_nl Y_lm and
+ * a = -grad Phi at each particle of posm (the masses are ignored).
+ * out_mask: ETICS_OUT_ACC | ETICS_OUT_POT (at least one); components not
+ * requested are written as 0.  Needs no workspace. */
+int etics_scf_field(const void *posm, int64_t N, int n_max, int l_max, int precision,
+                    const double *coeffs, void *accpot, int out_mask, void *stream);
+
+/* MEX force calculation (Sec. 2.3 eqs. 13-15, Sec. 3.2): radial sort, inner
+ * and outer exclusive cumulative sums of m r^l Y_lm and m r^-(l+1) Y_lm, and
+ * Phi_i = -sum_l 4pi/(2l+1) sum_m [q_lm(i) r^-(l+1) + p_lm(i) r^l] Y_lm(x_i).
+ * The order is by r^2 = (x*x + y*y) + z*z evaluated in FP64 (bitwise as a
+ * CPU evaluates it), ties by particle index.  A particle at the origin sorts
+ * first, contributes no outer moment, and feels only the outer l <= 1 field.
+ * ws: at least etics_workspace_bytes(N, 0, l_max, ETICS_MEX, p). */
+int etics_mex_field(const void *posm, int64_t N, int l_max, int precision, void *accpot,
+                    int out_mask, void *ws, size_t ws_bytes, void *stream);
+
+/* The radial order MEX uses (Sec. 3.2, the sort): order[k] = index of the
+ * particle of rank k.  order: device uint32[N].  ws as for etics_mex_field. */
+int etics_radial_sort(const void *posm, int64_t N, int precision, uint32_t *order,
+                      void *ws, size_t ws_bytes, void *stream);
+
+/* One kick-drift-kick leapfrog step (Sec. 3.4, Sec. 5.4), in place:
+ *   v += dt/2 a;  x += dt v;  (a, Phi) = force(x) by `method`;  v += dt/2 a.
+ * accpot holds a(x) on entry and (a, Phi) at the new positions on exit.
+ * coeffs_out (nullable, SCF only): receives the new coefficients.
+ * ws: etics_workspace_bytes(N, n_max, l_max, method, precision) bytes. */
+int etics_leapfrog_step(void *posm, void *vel, void *accpot, int64_t N, double dt,
+                        int method, int n_max, int l_max, int precision, double *coeffs_out,
+                        void *ws, size_t ws_bytes, void *stream);
+
+/* Waits for `stream`, then returns and clears the device error word
+ * (ETICS_OK if no kernel reported a data error since the last call). */
+int etics_get_error(void *stream);
+
+/* Static description of a status code. */
+const char *etics_strerror(int status);
+
+/* Number of kernels this library has launched in this process. */
+uint64_t etics_launch_count(void);
+
+/* Profiling aid: when events is non-NULL, later calls record
+ * events[k] (cudaEvent_t) at stage boundaries on their stream:
+ *   SCF coeffs: 0 start, 1 after the coefficient kernel, 2 end;
+ *   SCF field : 0 start, 1 end;
+ *   MEX       : 0 start, 1 keys, 2 sorted, 3 tile sums, 4 carries, 5 end.
+ * n_events is the array length (recording stops at it).  NULL disables.
+ * Not thread-safe: for single-threaded benchmarking. */
+int etics_set_stage_events(void **events, int n_events);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,238 @@
+// etics_api.cu -- the C ABI of include/etics.h: argument validation,
+// workspace sizing, the device error word and dispatch to the kernels.
+#include <atomic>
+#include <mutex>
+
+#include "etics_internal.h"
+
+namespace {
+
+// The device error word: one per device (a __device__ variable lives on
+// every device the library is used on).  Host code only ever uses its device
+// address, fetched per device with cudaGetSymbolAddress.
+__device__ unsigned int g_error_word;
+
+std::mutex g_mutex;
+constexpr int kMaxDevices = 64;
+unsigned* g_err_ptr[kMaxDevices] = {};
+int g_num_sms[kMaxDevices] = {};
+std::atomic<uint64_t> g_launches{0};
+void** g_events = nullptr;
+int g_n_events = 0;
+
+int current_device_state(unsigned** err, int* num_sms) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return ETICS_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (!g_err_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_error_word) != cudaSuccess) return ETICS_ERR_CUDA;
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return ETICS_ERR_CUDA;
+        g_err_ptr[dev] = static_cast<unsigned*>(p);
+        g_num_sms[dev] = sms;
+    }
+    *err = g_err_ptr[dev];
+    *num_sms = g_num_sms[dev];
+    return ETICS_OK;
+}
+
+struct CtxHolder {
+    etics::LaunchCtx ctx;
+    uint64_t launches = 0;
+    ~CtxHolder() { g_launches += launches; }
+};
+
+int make_ctx(void* stream, CtxHolder& h) {
+    unsigned* err = nullptr;
+    int sms = 0;
+    const int rc = current_device_state(&err, &sms);
+    if (rc) return rc;
+    h.ctx.stream = static_cast<cudaStream_t>(stream);
+    h.ctx.err = err;
+    h.ctx.num_sms = sms;
+    h.ctx.launches = &h.launches;
+    h.ctx.events = g_events;
+    h.ctx.n_events = g_n_events;
+    return ETICS_OK;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+bool valid_precision(int p) { return p == ETICS_FP64 || p == ETICS_MIXED; }
+bool valid_n(int64_t N) { return N >= 0 && N < (int64_t(1) << 30); }
+
+int check_particles(const void* p, int64_t N) {
+    if (N > 0 && (!p || !aligned(p, 16))) return ETICS_ERR_ARG;
+    return ETICS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t etics_workspace_bytes(int64_t N, int n_max, int l_max, int method, int precision) {
+    if (!valid_n(N) || !valid_precision(precision) || n_max < 0 || l_max < 0) return 0;
+    unsigned* err = nullptr;
+    int sms = 0;
+    if (current_device_state(&err, &sms)) return 0;
+    if (method == ETICS_SCF) {
+        if (n_max > ETICS_NMAX_LIMIT || l_max > ETICS_LMAX_LIMIT) return 0;
+        return precision == ETICS_MIXED ? etics::scf_workspace_f32(N, n_max, l_max, sms)
+                                        : etics::scf_workspace_f64(N, n_max, l_max, sms);
+    }
+    if (method == ETICS_MEX) {
+        if (l_max > ETICS_MEX_LMAX_LIMIT) return 0;
+        return precision == ETICS_MIXED ? etics::mex_workspace_f32(N) : etics::mex_workspace_f64(N);
+    }
+    return 0;
+}
+
+int etics_scf_coeffs(const void* posm, int64_t N, int n_max, int l_max, int precision,
+                     double* coeffs, void* ws, size_t ws_bytes, void* stream) {
+    if (!valid_n(N) || !valid_precision(precision) || !coeffs || !aligned(coeffs, 8))
+        return ETICS_ERR_ARG;
+    if (n_max < 0 || l_max < 0) return ETICS_ERR_ARG;
+    if (n_max > ETICS_NMAX_LIMIT || l_max > ETICS_LMAX_LIMIT) return ETICS_ERR_UNSUPPORTED;
+    if (check_particles(posm, N)) return ETICS_ERR_ARG;
+    if (!ws || !aligned(ws, 256)) return ETICS_ERR_ARG;
+    if (ws_bytes < etics_workspace_bytes(N, n_max, l_max, ETICS_SCF, precision))
+        return ETICS_ERR_WORKSPACE;
+    CtxHolder h;
+    int rc = make_ctx(stream, h);
+    if (rc) return rc;
+    etics::stage_event(h.ctx, 0);
+    rc = precision == ETICS_MIXED
+             ? etics::scf_coeffs_f32(posm, N, n_max, l_max, coeffs, ws, h.ctx)
+             : etics::scf_coeffs_f64(posm, N, n_max, l_max, coeffs, ws, h.ctx);
+    etics::stage_event(h.ctx, 2);
+    return rc;
+}
+
+int etics_scf_field(const void* posm, int64_t N, int n_max, int l_max, int precision,
+                    const double* coeffs, void* accpot, int out_mask, void* stream) {
+    if (!valid_n(N) || !valid_precision(precision) || !coeffs || !aligned(coeffs, 8))
+        return ETICS_ERR_ARG;
+    if (n_max < 0 || l_max < 0) return ETICS_ERR_ARG;
+    if (n_max > ETICS_NMAX_LIMIT || l_max > ETICS_LMAX_LIMIT) return ETICS_ERR_UNSUPPORTED;
+    if ((out_mask & (ETICS_OUT_ACC | ETICS_OUT_POT)) == 0 || (out_mask & ~3)) return ETICS_ERR_ARG;
+    if (check_particles(posm, N) || check_particles(accpot, N)) return ETICS_ERR_ARG;
+    CtxHolder h;
+    int rc = make_ctx(stream, h);
+    if (rc) return rc;
+    etics::stage_event(h.ctx, 0);
+    rc = precision == ETICS_MIXED
+             ? etics::scf_field_f32(posm, N, n_max, l_max, coeffs, accpot, out_mask, h.ctx)
+             : etics::scf_field_f64(posm, N, n_max, l_max, coeffs, accpot, out_mask, h.ctx);
+    etics::stage_event(h.ctx, 1);
+    return rc;
+}
+
+int etics_mex_field(const void* posm, int64_t N, int l_max, int precision, void* accpot,
+                    int out_mask, void* ws, size_t ws_bytes, void* stream) {
+    if (!valid_n(N) || !valid_precision(precision) || l_max < 0) return ETICS_ERR_ARG;
+    if (l_max > ETICS_MEX_LMAX_LIMIT) return ETICS_ERR_UNSUPPORTED;
+    if ((out_mask & (ETICS_OUT_ACC | ETICS_OUT_POT)) == 0 || (out_mask & ~3)) return ETICS_ERR_ARG;
+    if (check_particles(posm, N) || check_particles(accpot, N)) return ETICS_ERR_ARG;
+    if (!ws || !aligned(ws, 256)) return ETICS_ERR_ARG;
+    if (ws_bytes < etics_workspace_bytes(N, 0, l_max, ETICS_MEX, precision))
+        return ETICS_ERR_WORKSPACE;
+    CtxHolder h;
+    int rc = make_ctx(stream, h);
+    if (rc) return rc;
+    return precision == ETICS_MIXED
+               ? etics::mex_field_f32(posm, N, l_max, accpot, out_mask, ws, h.ctx)
+               : etics::mex_field_f64(posm, N, l_max, accpot, out_mask, ws, h.ctx);
+}
+
+int etics_radial_sort(const void* posm, int64_t N, int precision, uint32_t* order, void* ws,
+                      size_t ws_bytes, void* stream) {
+    if (!valid_n(N) || !valid_precision(precision)) return ETICS_ERR_ARG;
+    if (check_particles(posm, N) || (N > 0 && (!order || !aligned(order, 4)))) return ETICS_ERR_ARG;
+    if (!ws || !aligned(ws, 256)) return ETICS_ERR_ARG;
+    if (ws_bytes < etics_workspace_bytes(N, 0, 0, ETICS_MEX, precision)) return ETICS_ERR_WORKSPACE;
+    CtxHolder h;
+    int rc = make_ctx(stream, h);
+    if (rc) return rc;
+    return precision == ETICS_MIXED ? etics::radial_order_f32(posm, N, order, ws, h.ctx)
+                                    : etics::radial_order_f64(posm, N, order, ws, h.ctx);
+}
+
+int etics_leapfrog_step(void* posm, void* vel, void* accpot, int64_t N, double dt, int method,
+                        int n_max, int l_max, int precision, double* coeffs_out, void* ws,
+                        size_t ws_bytes, void* stream) {
+    if (!valid_n(N) || !valid_precision(precision) || !(dt == dt)) return ETICS_ERR_ARG;
+    if (method != ETICS_SCF && method != ETICS_MEX) return ETICS_ERR_ARG;
+    if (n_max < 0 || l_max < 0) return ETICS_ERR_ARG;
+    if (method == ETICS_SCF && (n_max > ETICS_NMAX_LIMIT || l_max > ETICS_LMAX_LIMIT))
+        return ETICS_ERR_UNSUPPORTED;
+    if (method == ETICS_MEX && l_max > ETICS_MEX_LMAX_LIMIT) return ETICS_ERR_UNSUPPORTED;
+    if (check_particles(posm, N) || check_particles(vel, N) || check_particles(accpot, N))
+        return ETICS_ERR_ARG;
+    if (!ws || !aligned(ws, 256)) return ETICS_ERR_ARG;
+    if (coeffs_out && !aligned(coeffs_out, 8)) return ETICS_ERR_ARG;
+    const size_t need = etics_workspace_bytes(N, n_max, l_max, method, precision);
+    const size_t ncoef = (size_t)(n_max + 1) * (l_max + 1) * (l_max + 1);
+    const size_t coef_bytes = method == ETICS_SCF && !coeffs_out ? (ncoef * 8 + 255) / 256 * 256 : 0;
+    if (ws_bytes < need + coef_bytes) return ETICS_ERR_WORKSPACE;
+    CtxHolder h;
+    int rc = make_ctx(stream, h);
+    if (rc) return rc;
+    const bool mixed = precision == ETICS_MIXED;
+    rc = mixed ? etics::kick_drift_f32(posm, vel, accpot, N, dt, h.ctx)
+               : etics::kick_drift_f64(posm, vel, accpot, N, dt, h.ctx);
+    if (rc) return rc;
+    if (method == ETICS_SCF) {
+        // coefficients go to coeffs_out, or to the end of the workspace
+        double* c = coeffs_out ? coeffs_out
+                               : reinterpret_cast<double*>(static_cast<uint8_t*>(ws) + need);
+        rc = mixed ? etics::scf_coeffs_f32(posm, N, n_max, l_max, c, ws, h.ctx)
+                   : etics::scf_coeffs_f64(posm, N, n_max, l_max, c, ws, h.ctx);
+        if (rc) return rc;
+        rc = mixed ? etics::scf_field_f32(posm, N, n_max, l_max, c, accpot, 3, h.ctx)
+                   : etics::scf_field_f64(posm, N, n_max, l_max, c, accpot, 3, h.ctx);
+    } else {
+        rc = mixed ? etics::mex_field_f32(posm, N, l_max, accpot, 3, ws, h.ctx)
+                   : etics::mex_field_f64(posm, N, l_max, accpot, 3, ws, h.ctx);
+    }
+    if (rc) return rc;
+    return mixed ? etics::kick_f32(vel, accpot, N, dt, h.ctx)
+                 : etics::kick_f64(vel, accpot, N, dt, h.ctx);
+}
+
+int etics_get_error(void* stream) {
+    unsigned* err = nullptr;
+    int sms = 0;
+    if (current_device_state(&err, &sms)) return ETICS_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned host = 0;
+    if (cudaMemcpyAsync(&host, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return ETICS_ERR_CUDA;
+    if (cudaMemsetAsync(err, 0, sizeof(unsigned), s) != cudaSuccess) return ETICS_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return ETICS_ERR_CUDA;
+    return host ? -(int)host : ETICS_OK;
+}
+
+const char* etics_strerror(int status) {
+    switch (status) {
+        case ETICS_OK: return "ok";
+        case ETICS_ERR_ARG: return "invalid argument";
+        case ETICS_ERR_CUDA: return "CUDA runtime error";
+        case ETICS_ERR_WORKSPACE: return "workspace too small";
+        case ETICS_ERR_NONFINITE: return "non-finite input or FP32 overflow";
+        case ETICS_ERR_TIMEOUT: return "inter-block wait timed out";
+        case ETICS_ERR_UNSUPPORTED: return "parameters beyond the compiled limits";
+        default: return "unknown status";
+    }
+}
+
+uint64_t etics_launch_count(void) { return g_launches.load(); }
+
+int etics_set_stage_events(void** events, int n_events) {
+    if (n_events < 0 || (n_events > 0 && !events)) return ETICS_ERR_ARG;
+    g_events = n_events > 0 ? events : nullptr;
+    g_n_events = n_events;
+    return ETICS_OK;
+}
+
+}  // extern "C"

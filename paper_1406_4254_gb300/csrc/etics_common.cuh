@@ -1,0 +1,235 @@
+// etics_common.cuh -- types, compile-time tables and device helpers shared by
+// the sm_103a kernels of the SCF / MEX expansion force library.
+//
+// All basis constants are computed here at compile time (constexpr) from
+// their definitions; nothing is shared with the CPU oracle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "etics.h"
+
+namespace etics {
+
+constexpr int kNmaxLimit = ETICS_NMAX_LIMIT;   // 16
+constexpr int kLmaxLimit = ETICS_LMAX_LIMIT;   // 14
+constexpr int kMexLmaxLimit = ETICS_MEX_LMAX_LIMIT;
+constexpr double kPi = 3.14159265358979323846;
+
+// ---------------------------------------------------------------------------
+// particle vectors: float4 for the mixed path, 4 doubles (16-byte aligned,
+// loaded as two 16-byte halves) for the FP64 path
+// ---------------------------------------------------------------------------
+struct __align__(16) dvec4 { double x, y, z, w; };
+
+template <typename R> struct Vec4T;
+template <> struct Vec4T<float> { using type = float4; };
+template <> struct Vec4T<double> { using type = dvec4; };
+template <typename R> using Vec4 = typename Vec4T<R>::type;
+
+__device__ __forceinline__ float4 ld4(const float4* p) { return *p; }
+__device__ __forceinline__ dvec4 ld4(const dvec4* p) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+    double2 a = q[0], b = q[1];
+    return dvec4{a.x, a.y, b.x, b.y};
+}
+__device__ __forceinline__ void st4(float4* p, float4 v) { *p = v; }
+__device__ __forceinline__ void st4(dvec4* p, dvec4 v) {
+    double2* q = reinterpret_cast<double2*>(p);
+    q[0] = make_double2(v.x, v.y);
+    q[1] = make_double2(v.z, v.w);
+}
+template <typename R> __device__ __forceinline__ Vec4<R> mk4(R a, R b, R c, R d);
+template <> __device__ __forceinline__ float4 mk4<float>(float a, float b, float c, float d) {
+    return make_float4(a, b, c, d);
+}
+template <> __device__ __forceinline__ dvec4 mk4<double>(double a, double b, double c, double d) {
+    return dvec4{a, b, c, d};
+}
+
+// ---------------------------------------------------------------------------
+// device error word: the first data error wins (ETICS_ERR_* codes)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void report(unsigned* err, int code) {
+    if (err) atomicCAS(err, 0u, (unsigned)(-code));
+}
+
+__device__ __forceinline__ bool finite4(float a, float b, float c, float d) {
+    return isfinite(a) && isfinite(b) && isfinite(c) && isfinite(d);
+}
+__device__ __forceinline__ bool finite4(double a, double b, double c, double d) {
+    return isfinite(a) && isfinite(b) && isfinite(c) && isfinite(d);
+}
+
+// ---------------------------------------------------------------------------
+// compile-time tables
+// ---------------------------------------------------------------------------
+constexpr double csqrt(double x) {
+    if (x <= 0.0) return 0.0;
+    double g = x > 1.0 ? x : 1.0;
+    for (int i = 0; i < 400; ++i) {
+        double ng = 0.5 * (g + x / g);
+        if (ng == g) break;
+        g = ng;
+    }
+    return g;
+}
+
+struct BasisTables {
+    // Gegenbauer recursion C_n = a[l][n] xi C_{n-1} - b[l][n] C_{n-2}, alpha = 2l + 3/2:
+    //   a = 2 (n + alpha - 1) / n,  b = (n + 2 alpha - 2) / n   (n >= 1; C_{-1} = 0)
+    float ga_f[kLmaxLimit + 1][kNmaxLimit + 1];
+    float gb_f[kLmaxLimit + 1][kNmaxLimit + 1];
+    double ga_d[kLmaxLimit + 1][kNmaxLimit + 1];
+    double gb_d[kLmaxLimit + 1][kNmaxLimit + 1];
+    // real orthonormal normalisation of the unnormalised harmonics used on
+    // the GPU (Re/Im of r^l P_l^m e^{i m phi}):  K_lm = sqrt((2l+1)/(4 pi)
+    // (l-m)!/(l+m)!), times sqrt2 for m > 0.  Indexed [l*(l+1)/2 + m], m >= 0.
+    double knorm[(kLmaxLimit + 1) * (kLmaxLimit + 2) / 2];
+    // MEX weights 4pi/(2l+1) K_lm^2 = (l-m)!/(l+m)! (times 2 for m > 0)
+    float mexw_f[(kLmaxLimit + 1) * (kLmaxLimit + 2) / 2];
+    double mexw_d[(kLmaxLimit + 1) * (kLmaxLimit + 2) / 2];
+    // 1/J_nl, J_nl = -K_nl (n+4l+2)!/n! / (2^(8l+6) (n+2l+3/2) pi prod_{k=0}^{2l}(k+1/2)^2),
+    // K_nl = n(n+4l+3)/2 + (l+1)(2l+1)
+    double inv_j[kNmaxLimit + 1][kLmaxLimit + 1];
+};
+
+constexpr BasisTables make_tables() {
+    BasisTables t{};
+    for (int l = 0; l <= kLmaxLimit; ++l) {
+        const double alpha = 2.0 * l + 1.5;
+        for (int n = 0; n <= kNmaxLimit; ++n) {
+            double a = 0.0, b = 0.0;
+            if (n >= 1) {
+                a = 2.0 * (n + alpha - 1.0) / n;
+                b = (n + 2.0 * alpha - 2.0) / n;
+            }
+            t.ga_d[l][n] = a;
+            t.gb_d[l][n] = b;
+            t.ga_f[l][n] = (float)a;
+            t.gb_f[l][n] = (float)b;
+        }
+        for (int m = 0; m <= l; ++m) {
+            double ratio = 1.0;   // (l-m)!/(l+m)!
+            for (int k = l - m + 1; k <= l + m; ++k) ratio /= (double)k;
+            const int idx = l * (l + 1) / 2 + m;
+            double k2 = (2.0 * l + 1.0) / (4.0 * kPi) * ratio * (m > 0 ? 2.0 : 1.0);
+            t.knorm[idx] = csqrt(k2);
+            const double w = ratio * (m > 0 ? 2.0 : 1.0);
+            t.mexw_d[idx] = w;
+            t.mexw_f[idx] = (float)w;
+        }
+    }
+    for (int n = 0; n <= kNmaxLimit; ++n) {
+        for (int l = 0; l <= kLmaxLimit; ++l) {
+            const double K = 0.5 * n * (n + 4.0 * l + 3.0) + (l + 1.0) * (2.0 * l + 1.0);
+            double num = 1.0;
+            for (int k = n + 1; k <= n + 4 * l + 2; ++k) num *= (double)k;
+            double den = (n + 2.0 * l + 1.5) * kPi;
+            for (int k = 0; k <= 2 * l; ++k) den *= (k + 0.5) * (k + 0.5);
+            for (int k = 0; k < 8 * l + 6; ++k) den *= 2.0;
+            const double J = -K * num / den;
+            t.inv_j[n][l] = 1.0 / J;
+        }
+    }
+    return t;
+}
+
+static __constant__ BasisTables c_tab = make_tables();
+
+template <typename R> __device__ __forceinline__ R geg_a(int l, int n);
+template <> __device__ __forceinline__ float geg_a<float>(int l, int n) { return c_tab.ga_f[l][n]; }
+template <> __device__ __forceinline__ double geg_a<double>(int l, int n) { return c_tab.ga_d[l][n]; }
+template <typename R> __device__ __forceinline__ R geg_b(int l, int n);
+template <> __device__ __forceinline__ float geg_b<float>(int l, int n) { return c_tab.gb_f[l][n]; }
+template <> __device__ __forceinline__ double geg_b<double>(int l, int n) { return c_tab.gb_d[l][n]; }
+template <typename R> __device__ __forceinline__ R mex_w(int idx);
+template <> __device__ __forceinline__ float mex_w<float>(int idx) { return c_tab.mexw_f[idx]; }
+template <> __device__ __forceinline__ double mex_w<double>(int idx) { return c_tab.mexw_d[idx]; }
+
+// ---------------------------------------------------------------------------
+// Unnormalised solid harmonics at a point u (used at the unit vector):
+//   Z_l^m(u) = |u|^l P_l^m(cos t) e^{i m phi} (no Condon-Shortley phase),
+//   C_l^m = Re Z_l^m, S_l^m = Im Z_l^m, m = 0..l.
+// Cartesian l-upward recursion (the stable direction, no cot(theta)):
+//   Z_m^m     = (2m-1) (ux + i uy) Z_{m-1}^{m-1}
+//   Z_{m+1}^m = (2m+1) uz Z_m^m
+//   (l-m) Z_l^m = (2l-1) uz Z_{l-1}^m - (l+m-1) |u|^2 Z_{l-2}^m
+// Gradient (homogeneous of degree l-1) from level l-1 by the ladder relations
+//   d/dz Z_l^m = (l+m) Z_{l-1}^m,
+//   (d/dx - i d/dy) Z_l^m = (l+m)(l+m-1) Z_{l-1}^{m-1},
+//   (d/dx + i d/dy) Z_l^m = -Z_{l-1}^{m+1}   (m >= 1),
+// and for m = 0: grad C_l^0 = (-C_{l-1}^1, -S_{l-1}^1, l C_{l-1}^0).
+// Arrays are indexed by m and must be used with compile-time l (unrolled).
+// ---------------------------------------------------------------------------
+template <typename R, int L>
+__device__ __forceinline__ void harm_level(const R* C1, const R* S1, const R* C2, const R* S2,
+                                           R ux, R uy, R uz, R uu, R* C, R* S) {
+    if constexpr (L == 0) {
+        C[0] = R(1);
+        S[0] = R(0);
+    } else {
+        constexpr R d = R(2 * L - 1);
+        C[L] = d * (ux * C1[L - 1] - uy * S1[L - 1]);
+        S[L] = d * (ux * S1[L - 1] + uy * C1[L - 1]);
+        C[L - 1] = d * uz * C1[L - 1];
+        S[L - 1] = (L - 1 == 0) ? R(0) : d * uz * S1[L - 1];
+#pragma unroll
+        for (int m = 0; m + 2 <= L; ++m) {
+            const R a = R(2 * L - 1) / R(L - m);
+            const R b = R(L + m - 1) / R(L - m);
+            C[m] = a * uz * C1[m] - b * uu * C2[m];
+            S[m] = (m == 0) ? R(0) : a * uz * S1[m] - b * uu * S2[m];
+        }
+    }
+}
+
+// gradient of C_L^m (gc) and S_L^m (gs) from level L-1 values (C1, S1; m <= L-1)
+template <typename R, int L>
+__device__ __forceinline__ void harm_grad(const R* C1, const R* S1, int m, R gc[3], R gs[3]) {
+    // values of level L-1 outside 0..L-1 are zero
+    auto c1 = [&](int k) -> R { return (k >= 0 && k <= L - 1) ? C1[k] : R(0); };
+    auto s1 = [&](int k) -> R { return (k >= 1 && k <= L - 1) ? S1[k] : R(0); };
+    if (m == 0) {
+        gc[0] = -c1(1);
+        gc[1] = -s1(1);
+        gc[2] = R(L) * c1(0);
+        gs[0] = gs[1] = gs[2] = R(0);
+    } else {
+        const R a = R((L + m) * (L + m - 1));
+        gc[0] = R(0.5) * (a * c1(m - 1) - c1(m + 1));
+        gc[1] = R(-0.5) * (a * s1(m - 1) + s1(m + 1));
+        gc[2] = R(L + m) * c1(m);
+        gs[0] = R(0.5) * (a * s1(m - 1) - s1(m + 1));
+        gs[1] = R(0.5) * (a * c1(m - 1) + c1(m + 1));
+        gs[2] = R(L + m) * s1(m);
+    }
+}
+
+// column layout of one harmonic level: col 0 = C_l^0, col 2m-1 = C_l^m,
+// col 2m = S_l^m (m >= 1); 2l+1 columns, padded to a multiple of 4.
+__host__ __device__ __forceinline__ int ncol_pad(int l) { return ((2 * l + 1 + 3) / 4) * 4; }
+__host__ __device__ __forceinline__ int col_offset(int l) {
+    int o = 0;
+    for (int k = 0; k < l; ++k) o += ncol_pad(k);
+    return o;
+}
+__host__ __device__ __forceinline__ int col_total(int lmax) { return col_offset(lmax + 1); }
+
+// launch context handed from the C ABI to the kernel launchers
+struct LaunchCtx {
+    cudaStream_t stream;
+    unsigned* err;        // device error word
+    int num_sms;
+    uint64_t* launches;   // host launch counter
+    void** events;        // stage events (nullable)
+    int n_events;
+};
+
+inline void stage_event(const LaunchCtx& ctx, int k) {
+    if (ctx.events && k < ctx.n_events && ctx.events[k])
+        cudaEventRecord((cudaEvent_t)ctx.events[k], ctx.stream);
+}
+
+}  // namespace etics

@@ -1,0 +1,53 @@
+// etics_internal.h -- declarations shared between the C ABI (etics_api.cu)
+// and the kernel translation units.
+#pragma once
+
+#include "etics_common.cuh"
+
+namespace etics {
+
+// ---- SCF (etics_scf_f32.cu / etics_scf_f64.cu) ----------------------------
+size_t scf_workspace_f32(int64_t N, int n_max, int l_max, int num_sms);
+size_t scf_workspace_f64(int64_t N, int n_max, int l_max, int num_sms);
+int scf_coeffs_f32(const void* posm, int64_t N, int n_max, int l_max, double* coeffs, void* ws,
+                   const LaunchCtx& ctx);
+int scf_coeffs_f64(const void* posm, int64_t N, int n_max, int l_max, double* coeffs, void* ws,
+                   const LaunchCtx& ctx);
+int scf_field_f32(const void* posm, int64_t N, int n_max, int l_max, const double* coeffs,
+                  void* out, int out_mask, const LaunchCtx& ctx);
+int scf_field_f64(const void* posm, int64_t N, int n_max, int l_max, const double* coeffs,
+                  void* out, int out_mask, const LaunchCtx& ctx);
+
+// ---- radial sort (etics_sort.cu) -------------------------------------------
+struct SortBuffers {
+    uint32_t *keys_a, *keys_b, *vals_a, *vals_b, *lo;
+    uint32_t *hist, *status, *counters;
+    void* zero_base;
+    size_t zero_bytes;
+};
+// carve the sort buffers from ws (ws may be null to only compute *total)
+SortBuffers sort_buffers(void* ws, int64_t N, size_t* total);
+int sort_tiles(int64_t N);
+// keys + 4 radix passes + tie fix-up; the order ends in vals_a
+template <typename R>
+int radial_sort_impl(const void* posm, int64_t N, const SortBuffers& b, const LaunchCtx& ctx);
+
+// ---- MEX (etics_mex_f32.cu / etics_mex_f64.cu) ----------------------------
+size_t mex_workspace_f32(int64_t N);
+size_t mex_workspace_f64(int64_t N);
+int mex_field_f32(const void* posm, int64_t N, int l_max, void* out, int out_mask, void* ws,
+                  const LaunchCtx& ctx);
+int mex_field_f64(const void* posm, int64_t N, int l_max, void* out, int out_mask, void* ws,
+                  const LaunchCtx& ctx);
+int radial_order_f32(const void* posm, int64_t N, uint32_t* order, void* ws, const LaunchCtx& ctx);
+int radial_order_f64(const void* posm, int64_t N, uint32_t* order, void* ws, const LaunchCtx& ctx);
+
+// ---- leapfrog (etics_step.cu) ----------------------------------------------
+int kick_drift_f32(void* posm, void* vel, const void* acc, int64_t N, double dt,
+                   const LaunchCtx& ctx);
+int kick_drift_f64(void* posm, void* vel, const void* acc, int64_t N, double dt,
+                   const LaunchCtx& ctx);
+int kick_f32(void* vel, const void* acc, int64_t N, double dt, const LaunchCtx& ctx);
+int kick_f64(void* vel, const void* acc, int64_t N, double dt, const LaunchCtx& ctx);
+
+}  // namespace etics

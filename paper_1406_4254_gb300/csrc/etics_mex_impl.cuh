@@ -1,0 +1,486 @@
+// etics_mex_impl.cuh -- MEX kernels after the radial sort (templated on the
+// arithmetic type; instantiated in etics_mex_f32.cu / etics_mex_f64.cu).
+//
+// Method (paper Sec. 2.3 eqs. 13-15, the sorted cumulative sums of Sec. 2.2):
+//   q_lm(i) = sum_{j before i} m_j r_j^l Y_lm(j),  p_lm(i) = sum_{j after i} m_j r_j^-(l+1) Y_lm(j)
+//   Phi_i   = -sum_l 4pi/(2l+1) sum_m [q_lm(i) r_i^-(l+1) + p_lm(i) r_i^l] Y_lm(i)
+// and a_i = -grad Phi_i at fixed q, p.
+//
+// GB300 design (the paper ran one library scan per (l, m) and direction):
+//   pass 1  gathers the particles in radial order (sorted copy), and reduces
+//           each tile's moments m rho^l Y and m rho^-(l+1) Y (rho = r / s_t,
+//           s_t a power of two per tile, so FP32 never overflows) to FP64.
+//   carry   scans the per-tile FP64 sums in a fixed order: exclusive forward
+//           for the inner moments, exclusive reverse (a true suffix sum) for
+//           the outer ones -- deterministic.
+//   pass 2  recomputes the moments, scans them inside the tile (warp
+//           shuffles + shared memory, forward and reverse), evaluates the
+//           field at every particle from the exclusive q and p, and scatters
+//           (a, Phi) back to the caller's order.
+// All harmonics are the unnormalised Cartesian solid harmonics of
+// etics_common.cuh; the MEX weights (l-m)!/(l+m)! (x2 for m > 0) restore the
+// orthonormal normalisation and the 4pi/(2l+1) factor at once.
+#pragma once
+
+#include "etics_internal.h"
+
+namespace etics {
+
+constexpr int kMexThreads = 128;
+constexpr int kMexP = 8;                          // particles per thread (consecutive)
+constexpr int kMexTile = kMexThreads * kMexP;     // 1024
+constexpr int kMexLB = kMexLmaxLimit;             // compiled level bound (6)
+constexpr int kMexNC = (kMexLB + 1) * (kMexLB + 1);
+
+inline int mex_tiles(int64_t N) { return (int)((N + kMexTile - 1) / kMexTile); }
+
+// tile scale exponent: s_t = 2^e with e halfway (in log2) between the first
+// and last radius of the tile (first radius 0 -> use the last)
+template <typename R>
+__device__ __forceinline__ int tile_exponent(R r_first, R r_last) {
+    if (!(r_last > R(0))) return 0;
+    const int el = ilogb(r_last);
+    const int ef = r_first > R(0) ? ilogb(r_first) : el;
+    const int s = ef + el;
+    return s >= 0 ? s / 2 : -((-s + 1) / 2);
+}
+
+template <typename R>
+__device__ __forceinline__ R radius(R x, R y, R z) {
+    return sqrt(x * x + y * y + z * z);
+}
+
+template <typename R>
+struct MexParticle {
+    R ux, uy, uz, uu, rho, m;
+    bool origin;
+    __device__ __forceinline__ void init(const Vec4<R>& v, R scale) {
+        const R r = radius<R>(v.x, v.y, v.z);
+        origin = !(r > R(0));
+        const R inv = origin ? R(0) : R(1) / r;
+        ux = v.x * inv; uy = v.y * inv; uz = v.z * inv;
+        uu = ux * ux + uy * uy + uz * uz;
+        rho = r * scale;
+        m = v.w;
+    }
+};
+
+// moment of column c of level L: index L*L + c
+template <typename R, int L>
+__device__ __forceinline__ R harm_col(const R* C, const R* S, int c) {
+    return c == 0 ? C[0] : ((c & 1) ? C[(c + 1) / 2] : S[c / 2]);
+}
+
+// ---- moments of one particle added to (ain, aout) ------------------------
+template <typename R, int L>
+__device__ __forceinline__ void mex_moments(R (&C)[3][kMexLB + 1], R (&S)[3][kMexLB + 1],
+                                            const MexParticle<R>& pt, int l_max, R win, R wout,
+                                            R irho, R (&ain)[kMexNC], R (&aout)[kMexNC]) {
+    if constexpr (L <= kMexLB) {
+        if (L > l_max) return;
+        constexpr int s0 = L % 3, s1 = (L + 2) % 3, s2 = (L + 1) % 3;
+        harm_level<R, L>(C[s1], S[s1], C[s2], S[s2], pt.ux, pt.uy, pt.uz, pt.uu, C[s0], S[s0]);
+#pragma unroll
+        for (int c = 0; c <= 2 * L; ++c) {
+            const R y = harm_col<R, L>(C[s0], S[s0], c);
+            ain[L * L + c] = fma(win, y, ain[L * L + c]);
+            aout[L * L + c] = fma(wout, y, aout[L * L + c]);
+        }
+        mex_moments<R, L + 1>(C, S, pt, l_max, win * pt.rho, wout * irho, irho, ain, aout);
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void particle_moments(const MexParticle<R>& pt, int l_max,
+                                                 R (&ain)[kMexNC], R (&aout)[kMexNC]) {
+    R C[3][kMexLB + 1], S[3][kMexLB + 1];
+    const R irho = pt.origin ? R(0) : R(1) / pt.rho;
+    // a particle at the origin has no outer moment (nothing lies inside it)
+    mex_moments<R, 0>(C, S, pt, l_max, pt.m, pt.origin ? R(0) : pt.m * irho, irho, ain, aout);
+}
+
+// ---- forward sweep: inner (q) part of the field, then q += own moment ------
+template <typename R, int L, bool ACC>
+__device__ __forceinline__ void mex_fwd(R (&C)[3][kMexLB + 1], R (&S)[3][kMexLB + 1],
+                                        const MexParticle<R>& pt, int l_max, R win, R rinv,
+                                        R irho, R (&q)[kMexNC], R& pot, R& ax, R& ay, R& az) {
+    if constexpr (L <= kMexLB) {
+        if (L > l_max) return;
+        constexpr int s0 = L % 3, s1 = (L + 2) % 3, s2 = (L + 1) % 3;
+        harm_level<R, L>(C[s1], S[s1], C[s2], S[s2], pt.ux, pt.uy, pt.uz, pt.uu, C[s0], S[s0]);
+        if (!pt.origin) {
+            R P = R(0), vx = R(0), vy = R(0), vz = R(0);
+#pragma unroll
+            for (int mm = 0; mm <= L; ++mm) {
+                const R w = mex_w<R>(L * (L + 1) / 2 + mm);
+                const R qc = w * q[L * L + (mm == 0 ? 0 : 2 * mm - 1)];
+                P = fma(qc, C[s0][mm], P);
+                R qs = R(0);
+                if (mm > 0) {
+                    qs = w * q[L * L + 2 * mm];
+                    P = fma(qs, S[s0][mm], P);
+                }
+                if (ACC && L >= 1) {
+                    R gc[3], gs[3];
+                    harm_grad<R, L>(C[s1], S[s1], mm, gc, gs);
+                    vx = fma(qc, gc[0], vx); vy = fma(qc, gc[1], vy); vz = fma(qc, gc[2], vz);
+                    if (mm > 0) { vx = fma(qs, gs[0], vx); vy = fma(qs, gs[1], vy); vz = fma(qs, gs[2], vz); }
+                }
+            }
+            // potential  -rho^-(l+1) P ;  a = rho^-(l+2) (V - (2l+1) P u)
+            pot = fma(rinv, P, pot);
+            if (ACC) {
+                const R f = rinv * irho;
+                const R k = R(2 * L + 1) * P;
+                ax = fma(f, vx - k * pt.ux, ax);
+                ay = fma(f, vy - k * pt.uy, ay);
+                az = fma(f, vz - k * pt.uz, az);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c <= 2 * L; ++c)
+            q[L * L + c] = fma(win, harm_col<R, L>(C[s0], S[s0], c), q[L * L + c]);
+        mex_fwd<R, L + 1, ACC>(C, S, pt, l_max, win * pt.rho, rinv * irho, irho, q, pot, ax, ay, az);
+    }
+}
+
+// ---- reverse sweep: outer (p) part of the field, then p += own moment ------
+template <typename R, int L, bool ACC>
+__device__ __forceinline__ void mex_rev(R (&C)[3][kMexLB + 1], R (&S)[3][kMexLB + 1],
+                                        const MexParticle<R>& pt, int l_max, R wout, R rl,
+                                        R rlm1, R irho, R (&p)[kMexNC], R& pot, R& ax, R& ay,
+                                        R& az) {
+    if constexpr (L <= kMexLB) {
+        if (L > l_max) return;
+        constexpr int s0 = L % 3, s1 = (L + 2) % 3, s2 = (L + 1) % 3;
+        harm_level<R, L>(C[s1], S[s1], C[s2], S[s2], pt.ux, pt.uy, pt.uz, pt.uu, C[s0], S[s0]);
+        R P = R(0), vx = R(0), vy = R(0), vz = R(0);
+#pragma unroll
+        for (int mm = 0; mm <= L; ++mm) {
+            const R w = mex_w<R>(L * (L + 1) / 2 + mm);
+            const R pc = w * p[L * L + (mm == 0 ? 0 : 2 * mm - 1)];
+            P = fma(pc, C[s0][mm], P);
+            R ps = R(0);
+            if (mm > 0) {
+                ps = w * p[L * L + 2 * mm];
+                P = fma(ps, S[s0][mm], P);
+            }
+            if (ACC && L >= 1) {
+                R gc[3], gs[3];
+                harm_grad<R, L>(C[s1], S[s1], mm, gc, gs);
+                vx = fma(pc, gc[0], vx); vy = fma(pc, gc[1], vy); vz = fma(pc, gc[2], vz);
+                if (mm > 0) { vx = fma(ps, gs[0], vx); vy = fma(ps, gs[1], vy); vz = fma(ps, gs[2], vz); }
+            }
+        }
+        // potential -rho^l P;  a = -grad: rho^(l-1) V (l >= 1)
+        pot = fma(rl, P, pot);
+        if (ACC && L >= 1) {
+            ax = fma(rlm1, vx, ax);
+            ay = fma(rlm1, vy, ay);
+            az = fma(rlm1, vz, az);
+        }
+#pragma unroll
+        for (int c = 0; c <= 2 * L; ++c)
+            p[L * L + c] = fma(wout, harm_col<R, L>(C[s0], S[s0], c), p[L * L + c]);
+        mex_rev<R, L + 1, ACC>(C, S, pt, l_max, wout * irho, rl * pt.rho, rl, irho, p, pot, ax, ay,
+                               az);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// pass 1: gather into radial order + per-tile FP64 moment sums
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(kMexThreads)
+mex_pass1_kernel(const Vec4<R>* __restrict__ posm, const uint32_t* __restrict__ perm, int64_t N,
+                 int l_max, Vec4<R>* __restrict__ sorted, double* __restrict__ tile_agg,
+                 unsigned* err) {
+    __shared__ R s_r[2];
+    __shared__ R s_red[kMexThreads / 32][2 * kMexNC];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t base = (int64_t)blockIdx.x * kMexTile;
+    const int64_t last = (base + kMexTile < N ? base + kMexTile : N) - 1;
+    Vec4<R> pp[kMexP];
+#pragma unroll
+    for (int k = 0; k < kMexP; ++k) {
+        const int64_t i = base + (int64_t)tid * kMexP + k;
+        if (i < N) {
+            pp[k] = ld4(posm + perm[i]);
+            if (!finite4(pp[k].x, pp[k].y, pp[k].z, pp[k].w)) {
+                report(err, ETICS_ERR_NONFINITE);
+                pp[k] = mk4<R>(R(0), R(0), R(0), R(0));
+            }
+            st4(sorted + i, pp[k]);
+            if (i == base) s_r[0] = radius<R>(pp[k].x, pp[k].y, pp[k].z);
+            if (i == last) s_r[1] = radius<R>(pp[k].x, pp[k].y, pp[k].z);
+        } else {
+            pp[k] = mk4<R>(R(0), R(0), R(0), R(0));
+        }
+    }
+    __syncthreads();
+    const int e = tile_exponent<R>(s_r[0], s_r[1]);
+    const R scale = ldexp(R(1), -e);
+    R ain[kMexNC], aout[kMexNC];
+#pragma unroll
+    for (int c = 0; c < kMexNC; ++c) { ain[c] = R(0); aout[c] = R(0); }
+#pragma unroll
+    for (int k = 0; k < kMexP; ++k) {
+        MexParticle<R> pt;
+        pt.init(pp[k], scale);
+        particle_moments<R>(pt, l_max, ain, aout);
+    }
+#pragma unroll
+    for (int c = 0; c < kMexNC; ++c) {
+        R a = ain[c], b = aout[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+        }
+        if (lane == 0) { s_red[warp][c] = a; s_red[warp][kMexNC + c] = b; }
+    }
+    __syncthreads();
+    for (int c = tid; c < 2 * kMexNC; c += kMexThreads) {
+        double s = 0.0;
+        for (int w = 0; w < kMexThreads / 32; ++w) s += (double)s_red[w][c];
+        const int cc = c % kMexNC;
+        int l = 0;
+        while ((l + 1) * (l + 1) <= cc) ++l;
+        // undo the tile scale: inner moments scale as s^l, outer as s^-(l+1)
+        s = (c < kMexNC) ? ldexp(s, l * e) : ldexp(s, -(l + 1) * e);
+        if (!isfinite(s)) report(err, ETICS_ERR_NONFINITE);
+        tile_agg[(size_t)blockIdx.x * 2 * kMexNC + c] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// carry: exclusive scans of the tile sums over tiles, one block per
+// component; forward for inner moments, reverse for outer (fixed order)
+// ---------------------------------------------------------------------------
+constexpr int kCarryThreads = 1024;
+static __global__ void __launch_bounds__(kCarryThreads)
+mex_carry_kernel(const double* __restrict__ tile_agg, int ntiles, double* __restrict__ carry) {
+    __shared__ double s_w[kCarryThreads / 32];
+    const int c = blockIdx.x;
+    const bool rev = c >= kMexNC;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int chunk = (ntiles + kCarryThreads - 1) / kCarryThreads;
+    const int o0 = tid * chunk;
+    auto tile_of = [&](int o) { return rev ? ntiles - 1 - o : o; };
+    double local = 0.0;
+    for (int o = o0; o < o0 + chunk && o < ntiles; ++o)
+        local += tile_agg[(size_t)tile_of(o) * 2 * kMexNC + c];
+    double x = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    double run = 0.0;
+    for (int w = 0; w < warp; ++w) run += s_w[w];
+    double ex = __shfl_up_sync(0xffffffffu, x, 1);
+    if (lane == 0) ex = 0.0;
+    run += ex;
+    for (int o = o0; o < o0 + chunk && o < ntiles; ++o) {
+        const size_t idx = (size_t)tile_of(o) * 2 * kMexNC + c;
+        carry[idx] = run;
+        run += tile_agg[idx];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// pass 2: in-tile scans + field + scatter
+// ---------------------------------------------------------------------------
+template <typename R, bool ACC>
+__global__ void __launch_bounds__(kMexThreads)
+mex_pass2_kernel(const Vec4<R>* __restrict__ sorted, const uint32_t* __restrict__ perm, int64_t N,
+                 int l_max, const double* __restrict__ carry, Vec4<R>* __restrict__ out,
+                 int out_mask, unsigned* err) {
+    constexpr int NW = kMexThreads / 32;
+    __shared__ R s_q0[kMexNC], s_p0[kMexNC];
+    __shared__ R s_wq[NW][kMexNC], s_wp[NW][kMexNC];
+    __shared__ int s_e;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t base = (int64_t)blockIdx.x * kMexTile;
+    const int64_t last = (base + kMexTile < N ? base + kMexTile : N) - 1;
+    if (tid == 0) {
+        const Vec4<R> a = ld4(sorted + base), b = ld4(sorted + last);
+        s_e = tile_exponent<R>(radius<R>(a.x, a.y, a.z), radius<R>(b.x, b.y, b.z));
+    }
+    __syncthreads();
+    const int e = s_e;
+    const R scale = ldexp(R(1), -e);
+    for (int c = tid; c < 2 * kMexNC; c += kMexThreads) {
+        const int cc = c % kMexNC;
+        int l = 0;
+        while ((l + 1) * (l + 1) <= cc) ++l;
+        const double v = carry[(size_t)blockIdx.x * 2 * kMexNC + c];
+        if (c < kMexNC) s_q0[cc] = (R)ldexp(v, -l * e);
+        else s_p0[cc] = (R)ldexp(v, (l + 1) * e);
+    }
+    Vec4<R> pp[kMexP];
+#pragma unroll
+    for (int k = 0; k < kMexP; ++k) {
+        const int64_t i = base + (int64_t)tid * kMexP + k;
+        pp[k] = (i < N) ? ld4(sorted + i) : mk4<R>(R(0), R(0), R(0), R(0));
+    }
+    // thread sums of the inner and outer moments
+    R a[kMexNC], b[kMexNC];
+#pragma unroll
+    for (int c = 0; c < kMexNC; ++c) { a[c] = R(0); b[c] = R(0); }
+#pragma unroll
+    for (int k = 0; k < kMexP; ++k) {
+        MexParticle<R> pt;
+        pt.init(pp[k], scale);
+        particle_moments<R>(pt, l_max, a, b);
+    }
+    // warp scans: exclusive prefix of a (forward), exclusive suffix of b (reverse)
+#pragma unroll
+    for (int c = 0; c < kMexNC; ++c) {
+        R x = a[c], y = b[c];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const R tx = __shfl_up_sync(0xffffffffu, x, o);
+            const R ty = __shfl_down_sync(0xffffffffu, y, o);
+            if (lane >= o) x += tx;
+            if (lane + o < 32) y += ty;
+        }
+        if (lane == 31) s_wq[warp][c] = x;
+        if (lane == 0) s_wp[warp][c] = y;
+        R ex = __shfl_up_sync(0xffffffffu, x, 1);
+        R ey = __shfl_down_sync(0xffffffffu, y, 1);
+        a[c] = (lane == 0) ? R(0) : ex;
+        b[c] = (lane == 31) ? R(0) : ey;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < kMexNC; ++c) {
+        R q0 = s_q0[c], p0 = s_p0[c];
+        for (int w = 0; w < warp; ++w) q0 += s_wq[w][c];
+        for (int w = NW - 1; w > warp; --w) p0 += s_wp[w][c];
+        a[c] = q0 + a[c];
+        b[c] = p0 + b[c];
+    }
+    // forward sweep (inner part of the field), reverse sweep (outer part)
+    R fpot[kMexP], fax[kMexP], fay[kMexP], faz[kMexP];
+#pragma unroll
+    for (int k = 0; k < kMexP; ++k) {
+        MexParticle<R> pt;
+        pt.init(pp[k], scale);
+        const R irho = pt.origin ? R(0) : R(1) / pt.rho;
+        R C[3][kMexLB + 1], S[3][kMexLB + 1];
+        fpot[k] = fax[k] = fay[k] = faz[k] = R(0);
+        mex_fwd<R, 0, ACC>(C, S, pt, l_max, pt.m, irho, irho, a, fpot[k], fax[k], fay[k], faz[k]);
+    }
+#pragma unroll
+    for (int k = kMexP - 1; k >= 0; --k) {
+        MexParticle<R> pt;
+        pt.init(pp[k], scale);
+        const R irho = pt.origin ? R(0) : R(1) / pt.rho;
+        R C[3][kMexLB + 1], S[3][kMexLB + 1];
+        const R wout = pt.origin ? R(0) : pt.m * irho;
+        mex_rev<R, 0, ACC>(C, S, pt, l_max, wout, R(1), R(0), irho, b, fpot[k], fax[k], fay[k],
+                           faz[k]);
+    }
+    // back to physical units: Phi = -F / s, a = grad-part / s^2; scatter
+    const R s1 = scale, s2 = scale * scale;
+#pragma unroll
+    for (int k = 0; k < kMexP; ++k) {
+        const int64_t i = base + (int64_t)tid * kMexP + k;
+        if (i < N) {
+            const R pot = (out_mask & ETICS_OUT_POT) ? -fpot[k] * s1 : R(0);
+            const R ax = ACC ? fax[k] * s2 : R(0);
+            const R ay = ACC ? fay[k] * s2 : R(0);
+            const R az = ACC ? faz[k] * s2 : R(0);
+            if (!finite4(ax, ay, az, pot)) report(err, ETICS_ERR_NONFINITE);
+            st4(out + perm[i], mk4<R>(ax, ay, az, pot));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+template <typename R>
+struct MexBuffers {
+    SortBuffers sort;
+    Vec4<R>* sorted;
+    double* tile_agg;
+    double* carry;
+};
+
+template <typename R>
+inline MexBuffers<R> mex_buffers(void* ws, int64_t N, size_t* total) {
+    MexBuffers<R> b{};
+    size_t off = 0;
+    b.sort = sort_buffers(ws, N, &off);
+    uint8_t* p = reinterpret_cast<uint8_t*>(ws);
+    auto take = [&](size_t bytes) {
+        uint8_t* q = p ? p + off : nullptr;
+        off += (bytes + 255) / 256 * 256;
+        return q;
+    };
+    const size_t n = (size_t)(N > 0 ? N : 1);
+    const size_t nt = (size_t)(mex_tiles(N) > 0 ? mex_tiles(N) : 1);
+    b.sorted = reinterpret_cast<Vec4<R>*>(take(n * sizeof(Vec4<R>)));
+    b.tile_agg = reinterpret_cast<double*>(take(nt * 2 * kMexNC * sizeof(double)));
+    b.carry = reinterpret_cast<double*>(take(nt * 2 * kMexNC * sizeof(double)));
+    if (total) *total = off;
+    return b;
+}
+
+template <typename R>
+inline size_t mex_workspace_impl(int64_t N) {
+    size_t total = 0;
+    mex_buffers<R>(nullptr, N, &total);
+    return total;
+}
+
+template <typename R>
+inline int mex_field_impl(const void* posm, int64_t N, int l_max, void* out, int out_mask,
+                          void* ws, const LaunchCtx& ctx) {
+    if (N == 0) return ETICS_OK;
+    MexBuffers<R> b = mex_buffers<R>(ws, N, nullptr);
+    stage_event(ctx, 0);
+    int rc = radial_sort_impl<R>(posm, N, b.sort, ctx);
+    if (rc) return rc;
+    stage_event(ctx, 2);
+    const int nt = mex_tiles(N);
+    const Vec4<R>* pp = reinterpret_cast<const Vec4<R>*>(posm);
+    mex_pass1_kernel<R><<<nt, kMexThreads, 0, ctx.stream>>>(pp, b.sort.vals_a, N, l_max, b.sorted,
+                                                            b.tile_agg, ctx.err);
+    if (cudaGetLastError()) return ETICS_ERR_CUDA;
+    ++*ctx.launches;
+    stage_event(ctx, 3);
+    mex_carry_kernel<<<2 * kMexNC, kCarryThreads, 0, ctx.stream>>>(b.tile_agg, nt, b.carry);
+    if (cudaGetLastError()) return ETICS_ERR_CUDA;
+    ++*ctx.launches;
+    stage_event(ctx, 4);
+    Vec4<R>* op = reinterpret_cast<Vec4<R>*>(out);
+    if (out_mask & ETICS_OUT_ACC)
+        mex_pass2_kernel<R, true><<<nt, kMexThreads, 0, ctx.stream>>>(
+            b.sorted, b.sort.vals_a, N, l_max, b.carry, op, out_mask, ctx.err);
+    else
+        mex_pass2_kernel<R, false><<<nt, kMexThreads, 0, ctx.stream>>>(
+            b.sorted, b.sort.vals_a, N, l_max, b.carry, op, out_mask, ctx.err);
+    if (cudaGetLastError()) return ETICS_ERR_CUDA;
+    ++*ctx.launches;
+    stage_event(ctx, 5);
+    return ETICS_OK;
+}
+
+template <typename R>
+inline int radial_order_impl(const void* posm, int64_t N, uint32_t* order, void* ws,
+                             const LaunchCtx& ctx) {
+    if (N == 0) return ETICS_OK;
+    MexBuffers<R> b = mex_buffers<R>(ws, N, nullptr);
+    int rc = radial_sort_impl<R>(posm, N, b.sort, ctx);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(order, b.sort.vals_a, (size_t)N * 4, cudaMemcpyDeviceToDevice, ctx.stream))
+        return ETICS_ERR_CUDA;
+    return ETICS_OK;
+}
+
+}  // namespace etics

@@ -1,0 +1,281 @@
+// etics_sort.cu -- the radial sort of MEX (paper Sec. 2.2: the cumulative
+// sums need the particles ordered by radius; Sec. 3.2 used a library merge
+// sort).
+//
+// GB300 design: a hand-written stable LSD radix sort (4 passes of 8 bits) of
+// the high 32 bits of the FP64 r^2 bit pattern, one kernel per pass
+// ("one-sweep": per-tile digit ranking with warp match + a decoupled
+// lookback over tiles for the digit offsets, scatter staged through shared
+// memory for coalesced writes).  Runs of equal high words are then ordered by
+// the low 32 bits and the particle index, which reproduces the exact FP64
+// order (r^2 = (x*x + y*y) + z*z rounded as a CPU does, ties by index).
+#include "etics_internal.h"
+
+namespace etics {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortKpt = 16;
+constexpr int kSortTile = kSortThreads * kSortKpt;   // 4096 keys per tile
+constexpr uint32_t kCountMask = (1u << 30) - 1;
+constexpr uint32_t kFlagAgg = 1u << 30;
+constexpr uint32_t kFlagInc = 2u << 30;
+constexpr int kSpinLimit = 1 << 22;
+constexpr int kMaxTieRun = 256;
+
+int sort_tiles(int64_t N) { return (int)((N + kSortTile - 1) / kSortTile); }
+
+// r^2 exactly as a CPU evaluates (x*x + y*y) + z*z in FP64, no contraction
+__device__ __forceinline__ double r2_fp64(double x, double y, double z) {
+    return __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z));
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256)
+keygen_kernel(const Vec4<R>* __restrict__ posm, int64_t N, uint32_t* __restrict__ key,
+              uint32_t* __restrict__ lo, uint32_t* __restrict__ val, uint32_t* __restrict__ hist,
+              unsigned* err) {
+    __shared__ uint32_t sh[4 * 256];
+    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const Vec4<R> v = ld4(posm + i);
+        uint64_t bits;
+        if (finite4(v.x, v.y, v.z, v.w)) {
+            bits = (uint64_t)__double_as_longlong(r2_fp64((double)v.x, (double)v.y, (double)v.z));
+        } else {
+            report(err, ETICS_ERR_NONFINITE);
+            bits = ~0ull;
+        }
+        const uint32_t hi = (uint32_t)(bits >> 32);
+        key[i] = hi;
+        lo[i] = (uint32_t)bits;
+        val[i] = (uint32_t)i;
+        atomicAdd(&sh[hi & 255], 1u);
+        atomicAdd(&sh[256 + ((hi >> 8) & 255)], 1u);
+        atomicAdd(&sh[512 + ((hi >> 16) & 255)], 1u);
+        atomicAdd(&sh[768 + (hi >> 24)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x)
+        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+// exclusive scan over the 256 threads of a block (one value per thread)
+__device__ __forceinline__ uint32_t block_excl_scan256(uint32_t v, uint32_t* s_warp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    uint32_t base = 0;
+    for (int w = 0; w < warp; ++w) base += s_warp[w];
+    __syncthreads();
+    return base + x - v;
+}
+
+__device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) {
+    return *reinterpret_cast<const volatile uint32_t*>(p);
+}
+__device__ __forceinline__ void st_volatile(uint32_t* p, uint32_t v) {
+    *reinterpret_cast<volatile uint32_t*>(p) = v;
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+                uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
+                const uint32_t* __restrict__ hist, uint32_t* status, uint32_t* counter, int shift,
+                int64_t N, unsigned* err) {
+    __shared__ uint32_t s_keys[kSortTile];
+    __shared__ uint32_t s_vals[kSortTile];
+    __shared__ uint32_t s_whist[kSortThreads / 32][256];
+    __shared__ uint32_t s_dexcl[256];
+    __shared__ uint32_t s_gbase[256];
+    __shared__ uint32_t s_scan[kSortThreads / 32];
+    __shared__ uint32_t s_tile;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_tile = atomicAdd(counter, 1u);
+    for (int i = tid; i < (kSortThreads / 32) * 256; i += kSortThreads) (&s_whist[0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const int64_t start = (int64_t)tile * kSortTile;
+
+    uint32_t k[kSortKpt], v[kSortKpt], d[kSortKpt], rank[kSortKpt];
+#pragma unroll
+    for (int s = 0; s < kSortKpt; ++s) {
+        const int64_t idx = start + (int64_t)warp * kSortKpt * 32 + s * 32 + lane;
+        if (idx < N) {
+            k[s] = keys_in[idx];
+            v[s] = vals_in[idx];
+            d[s] = (k[s] >> shift) & 255u;
+        } else {
+            k[s] = 0xffffffffu;
+            v[s] = 0;
+            d[s] = 256u;   // not a digit: out of range
+        }
+    }
+    // stable rank of every key among equal digits of this warp, in key order
+#pragma unroll
+    for (int s = 0; s < kSortKpt; ++s) {
+        const unsigned mask = __match_any_sync(0xffffffffu, d[s]);
+        const unsigned lower = mask & ((1u << lane) - 1u);
+        uint32_t before = 0;
+        if (d[s] < 256u) before = s_whist[warp][d[s]];
+        rank[s] = before + (uint32_t)__popc(lower);
+        __syncwarp();
+        if (d[s] < 256u && lower == 0u) s_whist[warp][d[s]] = before + (uint32_t)__popc(mask);
+        __syncwarp();
+    }
+    __syncthreads();
+    // per digit (one thread each): offsets over warps and the tile count
+    const int dig = tid;
+    uint32_t count = 0;
+    for (int w = 0; w < kSortThreads / 32; ++w) {
+        const uint32_t t = s_whist[w][dig];
+        s_whist[w][dig] = count;
+        count += t;
+    }
+    // decoupled lookback over earlier tiles for this digit
+    uint32_t* st = status + (size_t)tile * 256;
+    uint32_t excl = 0;
+    if (tile == 0) {
+        st_volatile(st + dig, kFlagInc | count);
+    } else {
+        st_volatile(st + dig, kFlagAgg | count);
+        int64_t t = (int64_t)tile - 1;
+        int spins = 0;
+        while (t >= 0) {
+            const uint32_t sv = ld_volatile(status + (size_t)t * 256 + dig);
+            if ((sv & ~kCountMask) == 0u) {
+                if (++spins > kSpinLimit) { report(err, ETICS_ERR_TIMEOUT); break; }
+                __nanosleep(32);
+                continue;
+            }
+            excl += sv & kCountMask;
+            if ((sv & ~kCountMask) == kFlagInc) break;
+            --t;
+        }
+        st_volatile(st + dig, kFlagInc | (excl + count));
+    }
+    // global start of each digit: exclusive scan of this pass's histogram
+    const uint32_t hexcl = block_excl_scan256(hist[dig], s_scan);
+    const uint32_t dexcl = block_excl_scan256(count, s_scan);
+    s_dexcl[dig] = dexcl;
+    s_gbase[dig] = hexcl + excl;
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < kSortKpt; ++s) {
+        if (d[s] < 256u) {
+            const uint32_t pos = s_dexcl[d[s]] + s_whist[warp][d[s]] + rank[s];
+            s_keys[pos] = k[s];
+            s_vals[pos] = v[s];
+        }
+    }
+    __syncthreads();
+    const int64_t rem = N - start;
+    const int nvalid = (int)(rem < kSortTile ? rem : kSortTile);
+    for (int i = tid; i < nvalid; i += kSortThreads) {
+        const uint32_t kk = s_keys[i];
+        const uint32_t dd = (kk >> shift) & 255u;
+        const uint32_t pos = s_gbase[dd] + (uint32_t)i - s_dexcl[dd];
+        keys_out[pos] = kk;
+        vals_out[pos] = s_vals[i];
+    }
+}
+
+// Runs of equal high words: order by (low word, index).  The run's first
+// element owns it; runs longer than kMaxTieRun are reported as unsupported.
+__global__ void tie_fixup_kernel(const uint32_t* __restrict__ key, const uint32_t* __restrict__ lo,
+                                 uint32_t* __restrict__ val, int64_t N, unsigned* err) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t k = key[i];
+        if (i > 0 && key[i - 1] == k) continue;
+        if (i + 1 >= N || key[i + 1] != k) continue;
+        int64_t j = i + 1;
+        while (j + 1 < N && key[j + 1] == k && j - i < kMaxTieRun) ++j;
+        if (j + 1 < N && key[j + 1] == k) { report(err, ETICS_ERR_UNSUPPORTED); continue; }
+        for (int64_t a = i + 1; a <= j; ++a) {
+            const uint32_t va = val[a];
+            const uint32_t la = lo[va];
+            int64_t b = a - 1;
+            while (b >= i) {
+                const uint32_t vb = val[b];
+                const uint32_t lb = lo[vb];
+                if (lb < la || (lb == la && vb < va)) break;
+                val[b + 1] = vb;
+                --b;
+            }
+            val[b + 1] = va;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+SortBuffers sort_buffers(void* ws, int64_t N, size_t* total) {
+    SortBuffers b{};
+    uint8_t* p = reinterpret_cast<uint8_t*>(ws);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        uint8_t* q = p ? p + off : nullptr;
+        off += (bytes + 255) / 256 * 256;
+        return q;
+    };
+    const size_t n4 = (size_t)(N > 0 ? N : 1) * 4;
+    b.keys_a = reinterpret_cast<uint32_t*>(take(n4));
+    b.keys_b = reinterpret_cast<uint32_t*>(take(n4));
+    b.vals_a = reinterpret_cast<uint32_t*>(take(n4));
+    b.vals_b = reinterpret_cast<uint32_t*>(take(n4));
+    b.lo = reinterpret_cast<uint32_t*>(take(n4));
+    const size_t nst = (size_t)sort_tiles(N);
+    b.zero_bytes = (4 * 256 + 4 * nst * 256 + 64) * 4;
+    b.zero_bytes = (b.zero_bytes + 255) / 256 * 256;
+    uint8_t* z = take(b.zero_bytes);
+    b.hist = reinterpret_cast<uint32_t*>(z);
+    b.status = b.hist ? b.hist + 4 * 256 : nullptr;
+    b.counters = b.status ? b.status + 4 * nst * 256 : nullptr;
+    b.zero_base = z;
+    if (total) *total = off;
+    return b;
+}
+
+template <typename R>
+int radial_sort_impl(const void* posm, int64_t N, const SortBuffers& b, const LaunchCtx& ctx) {
+    if (cudaMemsetAsync(b.zero_base, 0, b.zero_bytes, ctx.stream)) return ETICS_ERR_CUDA;
+    int kg = (int)((N + 255) / 256);
+    if (kg > ctx.num_sms * 8) kg = ctx.num_sms * 8;
+    keygen_kernel<R><<<kg, 256, 0, ctx.stream>>>(reinterpret_cast<const Vec4<R>*>(posm), N,
+                                                  b.keys_a, b.lo, b.vals_a, b.hist, ctx.err);
+    if (cudaGetLastError()) return ETICS_ERR_CUDA;
+    ++*ctx.launches;
+    stage_event(ctx, 1);
+    const int nst = sort_tiles(N);
+    uint32_t *kin = b.keys_a, *vin = b.vals_a, *kout = b.keys_b, *vout = b.vals_b;
+    for (int pass = 0; pass < 4; ++pass) {
+        onesweep_kernel<<<nst, kSortThreads, 0, ctx.stream>>>(
+            kin, vin, kout, vout, b.hist + pass * 256, b.status + (size_t)pass * nst * 256,
+            b.counters + pass, 8 * pass, N, ctx.err);
+        if (cudaGetLastError()) return ETICS_ERR_CUDA;
+        ++*ctx.launches;
+        uint32_t* t = kin; kin = kout; kout = t;
+        t = vin; vin = vout; vout = t;
+    }
+    // after 4 passes the sorted keys/values are back in keys_a / vals_a
+    int fg = (int)((N + 255) / 256);
+    if (fg > ctx.num_sms * 8) fg = ctx.num_sms * 8;
+    tie_fixup_kernel<<<fg, 256, 0, ctx.stream>>>(b.keys_a, b.lo, b.vals_a, N, ctx.err);
+    if (cudaGetLastError()) return ETICS_ERR_CUDA;
+    ++*ctx.launches;
+    return ETICS_OK;
+}
+
+template int radial_sort_impl<float>(const void*, int64_t, const SortBuffers&, const LaunchCtx&);
+template int radial_sort_impl<double>(const void*, int64_t, const SortBuffers&, const LaunchCtx&);
+
+}  // namespace etics

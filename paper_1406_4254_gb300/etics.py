@@ -1,0 +1,269 @@
+"""Thin Python binding of ``libetics.so`` (the C ABI in ``include/etics.h``).
+
+Argument marshalling only: every step of the force calculation runs in the
+library's CUDA kernels.  PyTorch supplies device memory and the current CUDA
+stream.  There is no CPU fallback: if the library is missing or no GPU is
+present the calls raise.
+
+Particle tensors are (N, 4) CUDA tensors (x, y, z, m): float32 selects the
+mixed-precision path, float64 the FP64 path.  Outputs are (N, 4) tensors
+(ax, ay, az, Phi) in the input's particle order.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+SCF, MEX = 0, 1
+FP64, MIXED = 0, 1
+OUT_ACC, OUT_POT = 1, 2
+NMAX_LIMIT, LMAX_LIMIT, MEX_LMAX_LIMIT = 16, 14, 6
+
+_STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA runtime error", -3: "workspace too small",
+           -4: "non-finite input or FP32 overflow", -5: "inter-block wait timed out",
+           -6: "parameters beyond the compiled limits"}
+
+_lock = threading.Lock()
+_lib = None
+_ws_cache: dict = {}
+
+
+class EticsError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {_STATUS.get(status, 'unknown')} ({status})")
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libetics.so (building it first if asked and needed)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_build.LIB):
+            if not build_if_missing:
+                raise RuntimeError(f"libetics.so not built ({_build.LIB})")
+            _build.build()
+        lib = ctypes.CDLL(_build.LIB)
+        vp, i64, i32, sz, dbl = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_size_t,
+                                 ctypes.c_double)
+        lib.etics_workspace_bytes.argtypes = [i64, i32, i32, i32, i32]
+        lib.etics_workspace_bytes.restype = sz
+        lib.etics_scf_coeffs.argtypes = [vp, i64, i32, i32, i32, vp, vp, sz, vp]
+        lib.etics_scf_field.argtypes = [vp, i64, i32, i32, i32, vp, vp, i32, vp]
+        lib.etics_mex_field.argtypes = [vp, i64, i32, i32, vp, i32, vp, sz, vp]
+        lib.etics_radial_sort.argtypes = [vp, i64, i32, vp, vp, sz, vp]
+        lib.etics_leapfrog_step.argtypes = [vp, vp, vp, i64, dbl, i32, i32, i32, i32, vp, vp, sz,
+                                            vp]
+        lib.etics_get_error.argtypes = [vp]
+        lib.etics_strerror.argtypes = [i32]
+        lib.etics_strerror.restype = ctypes.c_char_p
+        lib.etics_launch_count.restype = ctypes.c_uint64
+        lib.etics_set_stage_events.argtypes = [ctypes.POINTER(ctypes.c_void_p), i32]
+        for name in ("etics_scf_coeffs", "etics_scf_field", "etics_mex_field",
+                     "etics_radial_sort", "etics_leapfrog_step", "etics_get_error",
+                     "etics_set_stage_events"):
+            getattr(lib, name).restype = i32
+        _lib = lib
+        return lib
+
+
+def _stream(stream) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _precision(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return MIXED
+    if t.dtype == torch.float64:
+        return FP64
+    raise TypeError("particle arrays must be float32 (mixed) or float64 (FP64)")
+
+
+def _particles(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dim() != 2 or t.shape[1] != 4 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous (N, 4) tensor")
+    return t
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise EticsError(rc, what)
+
+
+def workspace_bytes(n: int, n_max: int, l_max: int, method: int, precision: int) -> int:
+    return int(load().etics_workspace_bytes(int(n), int(n_max), int(l_max), int(method),
+                                            int(precision)))
+
+
+def workspace(n: int, n_max: int, l_max: int, method: int, precision: int, device=None,
+              extra: int = 0) -> torch.Tensor:
+    """A cached uint8 device buffer large enough for the call."""
+    dev = torch.device(device) if device is not None else torch.device("cuda",
+                                                                        torch.cuda.current_device())
+    need = workspace_bytes(n, n_max, l_max, method, precision) + extra
+    if need <= 0:
+        raise EticsError(-1, "workspace_bytes")
+    key = (dev.index, method)
+    buf = _ws_cache.get(key)
+    if buf is None or buf.numel() < need:
+        buf = torch.empty(need + 256, dtype=torch.uint8, device=dev)
+        _ws_cache[key] = buf
+    return buf
+
+
+def _aligned_ptr(buf: torch.Tensor) -> tuple[int, int]:
+    p = buf.data_ptr()
+    q = (p + 255) // 256 * 256
+    return q, buf.numel() - (q - p)
+
+
+def scf_coeffs(posm: torch.Tensor, n_max: int, l_max: int, out: torch.Tensor | None = None,
+               ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """SCF coefficients c[n, l*l+l+m] (float64, shape (n_max+1, (l_max+1)^2))."""
+    posm = _particles(posm, "posm")
+    prec = _precision(posm)
+    n = posm.shape[0]
+    if out is None:
+        out = torch.empty((n_max + 1, (l_max + 1) ** 2), dtype=torch.float64, device=posm.device)
+    if ws is None:
+        ws = workspace(n, n_max, l_max, SCF, prec, posm.device)
+    wp, wb = _aligned_ptr(ws)
+    _check(load().etics_scf_coeffs(posm.data_ptr(), n, n_max, l_max, prec, out.data_ptr(), wp, wb,
+                                   _stream(stream)), "etics_scf_coeffs")
+    return out
+
+
+def scf_field(posm: torch.Tensor, coeffs: torch.Tensor, n_max: int, l_max: int,
+              out: torch.Tensor | None = None, out_mask: int = OUT_ACC | OUT_POT,
+              stream=None) -> torch.Tensor:
+    """SCF (ax, ay, az, Phi) at each particle of posm."""
+    posm = _particles(posm, "posm")
+    prec = _precision(posm)
+    if coeffs.dtype != torch.float64 or not coeffs.is_cuda or not coeffs.is_contiguous():
+        raise ValueError("coeffs must be a contiguous float64 CUDA tensor")
+    if coeffs.numel() != (n_max + 1) * (l_max + 1) ** 2:
+        raise ValueError("coefficient count does not match (n_max, l_max)")
+    if out is None:
+        out = torch.empty_like(posm)
+    _check(load().etics_scf_field(posm.data_ptr(), posm.shape[0], n_max, l_max, prec,
+                                  coeffs.data_ptr(), out.data_ptr(), out_mask, _stream(stream)),
+           "etics_scf_field")
+    return out
+
+
+def scf_force(posm: torch.Tensor, n_max: int, l_max: int, out=None, stream=None):
+    """Both SCF passes; returns (accpot, coeffs)."""
+    c = scf_coeffs(posm, n_max, l_max, stream=stream)
+    return scf_field(posm, c, n_max, l_max, out=out, stream=stream), c
+
+
+def mex_field(posm: torch.Tensor, l_max: int, out: torch.Tensor | None = None,
+              out_mask: int = OUT_ACC | OUT_POT, ws: torch.Tensor | None = None,
+              stream=None) -> torch.Tensor:
+    """MEX (ax, ay, az, Phi) at each particle."""
+    posm = _particles(posm, "posm")
+    prec = _precision(posm)
+    n = posm.shape[0]
+    if out is None:
+        out = torch.empty_like(posm)
+    if ws is None:
+        ws = workspace(n, 0, l_max, MEX, prec, posm.device)
+    wp, wb = _aligned_ptr(ws)
+    _check(load().etics_mex_field(posm.data_ptr(), n, l_max, prec, out.data_ptr(), out_mask, wp,
+                                  wb, _stream(stream)), "etics_mex_field")
+    return out
+
+
+def radial_order(posm: torch.Tensor, ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Particle indices in MEX's radial order (int64 tensor)."""
+    posm = _particles(posm, "posm")
+    prec = _precision(posm)
+    n = posm.shape[0]
+    order = torch.empty(max(n, 1), dtype=torch.int32, device=posm.device)
+    if ws is None:
+        ws = workspace(n, 0, 0, MEX, prec, posm.device)
+    wp, wb = _aligned_ptr(ws)
+    _check(load().etics_radial_sort(posm.data_ptr(), n, prec, order.data_ptr(), wp, wb,
+                                    _stream(stream)), "etics_radial_sort")
+    return order[:n].to(torch.int64) & 0xFFFFFFFF
+
+
+def leapfrog_step(posm: torch.Tensor, vel: torch.Tensor, accpot: torch.Tensor, dt: float,
+                  method: int, n_max: int, l_max: int, coeffs_out: torch.Tensor | None = None,
+                  ws: torch.Tensor | None = None, stream=None) -> None:
+    """One in-place KDK step; accpot holds a(x) on entry and (a, Phi) after."""
+    posm = _particles(posm, "posm")
+    vel = _particles(vel, "vel")
+    accpot = _particles(accpot, "accpot")
+    prec = _precision(posm)
+    if vel.dtype != posm.dtype or accpot.dtype != posm.dtype:
+        raise TypeError("posm, vel and accpot must share a dtype")
+    n = posm.shape[0]
+    extra = ((n_max + 1) * (l_max + 1) ** 2 * 8 + 255) // 256 * 256 if method == SCF else 0
+    if ws is None:
+        ws = workspace(n, n_max, l_max, method, prec, posm.device, extra=extra)
+    wp, wb = _aligned_ptr(ws)
+    cp = coeffs_out.data_ptr() if coeffs_out is not None else None
+    _check(load().etics_leapfrog_step(posm.data_ptr(), vel.data_ptr(), accpot.data_ptr(), n,
+                                      float(dt), method, n_max, l_max, prec, cp, wp, wb,
+                                      _stream(stream)), "etics_leapfrog_step")
+
+
+def get_error(stream=None) -> int:
+    """Synchronise the stream and return/clear the device error status."""
+    return int(load().etics_get_error(_stream(stream)))
+
+
+def check_error(stream=None):
+    rc = get_error(stream)
+    if rc:
+        raise EticsError(rc, "device")
+
+
+def launch_count() -> int:
+    return int(load().etics_launch_count())
+
+
+def set_stage_events(events) -> None:
+    """Record torch.cuda.Event objects at stage boundaries (None disables)."""
+    lib = load()
+    if not events:
+        _check(lib.etics_set_stage_events(None, 0), "etics_set_stage_events")
+        set_stage_events._keep = None
+        return
+    arr = (ctypes.c_void_p * len(events))(*[ctypes.c_void_p(e.cuda_event) for e in events])
+    set_stage_events._keep = arr
+    _check(lib.etics_set_stage_events(arr, len(events)), "etics_set_stage_events")
+
+
+def to_host_force(posm_host: torch.Tensor, method: int, n_max: int, l_max: int,
+                  out_host: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """End-to-end convenience: host (pinned) particles in, host (ax, ay, az, Phi) out.
+
+    Copies the particles to the device, runs the force calculation and copies
+    the result back, all on one stream."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    s = stream if stream is not None else torch.cuda.current_stream()
+    with torch.cuda.stream(s):
+        d = posm_host.to(dev, non_blocking=True)
+        if method == SCF:
+            res, _ = scf_force(d, n_max, l_max, stream=s)
+        else:
+            res = mex_field(d, l_max, stream=s)
+        if out_host is None:
+            out_host = torch.empty(res.shape, dtype=res.dtype, pin_memory=True)
+        out_host.copy_(res, non_blocking=True)
+    return out_host

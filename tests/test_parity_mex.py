@@ -1,0 +1,120 @@
+"""GPU MEX (radix sort + scans + field through the C ABI) against the FP64
+oracle (paper Sec. 2.3 eqs. 13-15 with the sort of Sec. 2.2).
+
+The radial order is integer work and must match bit for bit; fields are
+compared per particle with eq. 18's relative error."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from helpers import assert_field_close, device_particles, hernquist, rounded
+from paper_1406_4254_gb300 import etics
+
+pytestmark = pytest.mark.gpu
+
+
+def oracle_order(pm):
+    x = pm[:, :3]
+    r2 = (x[:, 0] * x[:, 0] + x[:, 1] * x[:, 1]) + x[:, 2] * x[:, 2]
+    return np.lexsort((np.arange(len(x)), r2))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("n", [1, 2, 3, 4095, 4096, 4097, 12345, 100003])
+def test_radial_order_is_exact(precision, n):
+    pm = hernquist(n, seed=n)
+    if n > 10:
+        # exact ties (mirror images) and tiny-gap near ties
+        pm[5, :3] = pm[3, :3] * np.array([-1.0, 1.0, -1.0])
+        pm[8, :3] = pm[3, :3][[1, 0, 2]]
+        pm[9, :3] = pm[3, :3] * (1 + 1e-15)
+    ref_in = rounded(pm, precision)
+    got = etics.radial_order(device_particles(pm, precision)).cpu().numpy()
+    etics.check_error()
+    ref = oracle_order(ref_in)
+    assert np.array_equal(got, ref)
+    _, _, o_or = oracle.mex_field(ref_in[:, :3], ref_in[:, 3], 0)
+    assert np.array_equal(o_or, ref)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_radial_order_full_size(precision):
+    n = 1 << 20
+    pm = hernquist(n, seed=0)
+    got = etics.radial_order(device_particles(pm, precision)).cpu().numpy()
+    etics.check_error()
+    assert np.array_equal(got, oracle_order(rounded(pm, precision)))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("l_max", [6, 4, 2, 1, 0])
+def test_field_matches_oracle(precision, l_max):
+    pm = hernquist(12345, seed=11)
+    ref_in = rounded(pm, precision)
+    acc_ref, pot_ref, _ = oracle.mex_field(ref_in[:, :3], ref_in[:, 3], l_max)
+    out = etics.mex_field(device_particles(pm, precision), l_max)
+    etics.check_error()
+    o = out.cpu().numpy()
+    # the innermost particle has no inner mass: its force is pure noise of the
+    # outer moments; compare all particles with the eq. 18 metric
+    assert_field_close(o, acc_ref, pot_ref, precision, f"mex l={l_max}")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_edge_cases(precision):
+    rng = np.random.default_rng(12)
+    cases = [np.array([[0.3, -0.2, 0.5, 1.0]]),
+             np.array([[0.0, 0.0, 0.0, 0.5], [1.0, 2.0, -1.0, 0.5]]),
+             np.array([[0.0, 0.0, 2.0, 0.3], [0.0, 0.0, -0.7, 0.3], [1e-3, 0.0, 0.0, 0.4]])]
+    big = hernquist(3000, seed=13)
+    big[:10, :2] = 0.0                 # on the z axis
+    big[10, :3] = 0.0                  # the origin
+    big[11, :3] = big[12, :3] * [-1, -1, 1]   # tie
+    big[100:140, 3] *= rng.uniform(0.5, 2.0, 40)
+    cases.append(big)
+    for pm in cases:
+        for l_max in [6, 3, 0]:
+            ref_in = rounded(pm, precision)
+            acc_ref, pot_ref, _ = oracle.mex_field(ref_in[:, :3], ref_in[:, 3], l_max)
+            o = etics.mex_field(device_particles(pm, precision), l_max).cpu().numpy()
+            etics.check_error()
+            amax = max(np.max(np.linalg.norm(acc_ref, axis=1)), 1e-300)
+            tol = 1e-11 if precision == "fp64" else 2e-5
+            assert np.max(np.abs(o[:, :3] - acc_ref)) <= tol * amax, (len(pm), l_max)
+            pmax = max(np.max(np.abs(pot_ref)), 1e-300)
+            assert np.max(np.abs(o[:, 3] - pot_ref)) <= tol * pmax, (len(pm), l_max)
+
+
+def test_output_masks_and_empty():
+    pm = hernquist(5000, seed=14)
+    d = device_particles(pm, "mixed")
+    both = etics.mex_field(d, 6).cpu().numpy()
+    pot = etics.mex_field(d, 6, out_mask=etics.OUT_POT).cpu().numpy()
+    acc = etics.mex_field(d, 6, out_mask=etics.OUT_ACC).cpu().numpy()
+    # the potential-only kernel is a separate instantiation: equal up to FP32 rounding
+    assert np.all(pot[:, :3] == 0)
+    np.testing.assert_allclose(pot[:, 3], both[:, 3], rtol=1e-6)
+    assert np.all(acc[:, 3] == 0) and np.array_equal(acc[:, :3], both[:, :3])
+    e = torch.zeros((0, 4), dtype=torch.float32, device="cuda")
+    etics.mex_field(e, 6)
+    etics.check_error()
+
+
+def test_deterministic():
+    d = device_particles(hernquist(50000, seed=15), "mixed")
+    a = etics.mex_field(d, 6)
+    b = etics.mex_field(d, 6)
+    assert torch.equal(a, b)
+
+
+def test_full_size_bench_config():
+    """N = 2^20 flattened Hernquist (1 : 0.8 : 0.6), l_max = 6, mixed path:
+    every particle against the oracle."""
+    n = 1 << 20
+    pm = hernquist(n, seed=0)
+    ref_in = rounded(pm, "mixed")
+    acc_ref, pot_ref, _ = oracle.mex_field(ref_in[:, :3], ref_in[:, 3], 6)
+    o = etics.mex_field(device_particles(pm, "mixed"), 6).cpu().numpy()
+    etics.check_error()
+    assert_field_close(o, acc_ref, pot_ref, "mixed", "mex 2^20")
