@@ -116,6 +116,34 @@ class Clocks:
                 "samples": len(rows)}
 
 
+# --- raw CUDA events (recorded inside the library on the call's stream) -------
+class RawEvents:
+    """cudaEvent_t handles created with the driver API, so that events the
+    library records can be timed (torch only times events it recorded)."""
+
+    def __init__(self, n):
+        import ctypes
+        self.ct = ctypes
+        self.cu = ctypes.CDLL("libcuda.so.1")
+        self.ev = []
+        for _ in range(n):
+            h = ctypes.c_void_p()
+            rc = self.cu.cuEventCreate(ctypes.byref(h), 0)
+            if rc != 0:
+                raise RuntimeError(f"cuEventCreate failed ({rc})")
+            self.ev.append(h)
+
+    def handles(self, a, b):
+        return [self.ct.c_void_p(h.value) for h in self.ev[a:b]]
+
+    def ms(self, i, j):
+        out = self.ct.c_float()
+        rc = self.cu.cuEventElapsedTime(self.ct.byref(out), self.ev[i], self.ev[j])
+        if rc != 0:
+            raise RuntimeError(f"cuEventElapsedTime failed ({rc})")
+        return float(out.value)
+
+
 # --- GPU arm -------------------------------------------------------------------
 def run_etics(args, rank, world):
     import torch
@@ -140,19 +168,20 @@ def run_etics(args, rank, world):
     ws_mex = etics.workspace(n, 0, L_MAX, etics.MEX, etics.MIXED, dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 126 MB L2
 
-    # stage events: [scf: 0 start, 1 coeff kernel end, 2 end][field 0,1][mex 0..5]
-    ev = {k: [torch.cuda.Event(enable_timing=True) for _ in range(6)]
-          for k in ("coef", "field", "mex")}
+    # stage events: 0-2 scf coeffs (start, coefficient kernel end, end),
+    # 3-4 scf field (start, end), 5-10 mex (start, keys, sorted, tile sums,
+    # carries, end)
+    rev = RawEvents(11)
 
     def step(timed_stages=False):
         if timed_stages:
-            etics.set_stage_events(ev["coef"][:3])
+            etics.set_stage_events(rev.handles(0, 3))
         etics.scf_coeffs(x, N_MAX, L_MAX, out=coeffs, ws=ws_scf)
         if timed_stages:
-            etics.set_stage_events(ev["field"][:2])
+            etics.set_stage_events(rev.handles(3, 5))
         etics.scf_field(x, coeffs, N_MAX, L_MAX, out=out_scf)
         if timed_stages:
-            etics.set_stage_events(ev["mex"])
+            etics.set_stage_events(rev.handles(5, 11))
         etics.mex_field(x, L_MAX, out=out_mex, ws=ws_mex)
         if timed_stages:
             etics.set_stage_events(None)
@@ -179,17 +208,16 @@ def run_etics(args, rank, world):
         t_end.record(stream)
         torch.cuda.synchronize()
         times.append(t_start.elapsed_time(t_end))
-        e = ev
-        stage["coef_kernel"].append(e["coef"][0].elapsed_time(e["coef"][1]))
-        stage["finalize"].append(e["coef"][1].elapsed_time(e["coef"][2]))
-        stage["field_kernel"].append(e["field"][0].elapsed_time(e["field"][1]))
-        stage["scf"].append(e["coef"][0].elapsed_time(e["field"][1]))
-        stage["mex_keys"].append(e["mex"][0].elapsed_time(e["mex"][1]))
-        stage["mex_sort"].append(e["mex"][1].elapsed_time(e["mex"][2]))
-        stage["mex_tile_sums"].append(e["mex"][2].elapsed_time(e["mex"][3]))
-        stage["mex_carry"].append(e["mex"][3].elapsed_time(e["mex"][4]))
-        stage["mex_pass2"].append(e["mex"][4].elapsed_time(e["mex"][5]))
-        stage["mex"].append(e["mex"][0].elapsed_time(e["mex"][5]))
+        stage["coef_kernel"].append(rev.ms(0, 1))
+        stage["finalize"].append(rev.ms(1, 2))
+        stage["field_kernel"].append(rev.ms(3, 4))
+        stage["scf"].append(rev.ms(0, 4))
+        stage["mex_keys"].append(rev.ms(5, 6))
+        stage["mex_sort"].append(rev.ms(6, 7))
+        stage["mex_tile_sums"].append(rev.ms(7, 8))
+        stage["mex_carry"].append(rev.ms(8, 9))
+        stage["mex_pass2"].append(rev.ms(9, 10))
+        stage["mex"].append(rev.ms(5, 10))
     torch.cuda.synchronize()
     clk = clocks.stop()
     launches = etics.launch_count() - l0

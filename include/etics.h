@@ -35,7 +35,7 @@
  *     FP32 overflow, a lookback wait that timed out) set a device error word
  *     that etics_get_error() reads.
  *   - Limits: 0 <= n_max <= ETICS_NMAX_LIMIT, 0 <= l_max <= ETICS_LMAX_LIMIT
- *     (SCF); 0 <= l_max <= ETICS_MEX_LMAX_LIMIT (MEX); N < 2^31.
+ *     (SCF); 0 <= l_max <= ETICS_MEX_LMAX_LIMIT (MEX); 0 <= N < 2^30.
  *   - Results are deterministic: the same inputs on the same device give
  *     bitwise identical outputs.
  */
@@ -105,6 +105,13 @@ int etics_mex_field(const void *posm, int64_t N, int l_max, int precision, void 
  * particle of rank k.  order: device uint32[N].  ws as for etics_mex_field. */
 int etics_radial_sort(const void *posm, int64_t N, int precision, uint32_t *order,
                       void *ws, size_t ws_bytes, void *stream);
+
+/* The radial sort key of every particle (the first step of the MEX sort):
+ * keys[i] = high 32 bits of the IEEE-754 FP64 bit pattern of
+ * r^2 = (x*x + y*y) + z*z evaluated in FP64 (as a CPU rounds it), for the
+ * particle's own coordinates (float4 coordinates are widened exactly).
+ * keys: device uint32[N].  Needs no workspace. */
+int etics_radial_keys(const void *posm, int64_t N, int precision, uint32_t *keys, void *stream);
 
 /* One kick-drift-kick leapfrog step (Sec. 3.4, Sec. 5.4), in place:
  *   v += dt/2 a;  x += dt v;  (a, Phi) = force(x) by `method`;  v += dt/2 a.

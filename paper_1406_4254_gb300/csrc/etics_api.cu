@@ -158,6 +158,16 @@ int etics_radial_sort(const void* posm, int64_t N, int precision, uint32_t* orde
                                     : etics::radial_order_f64(posm, N, order, ws, h.ctx);
 }
 
+int etics_radial_keys(const void* posm, int64_t N, int precision, uint32_t* keys, void* stream) {
+    if (!valid_n(N) || !valid_precision(precision)) return ETICS_ERR_ARG;
+    if (check_particles(posm, N) || (N > 0 && (!keys || !aligned(keys, 4)))) return ETICS_ERR_ARG;
+    CtxHolder h;
+    int rc = make_ctx(stream, h);
+    if (rc) return rc;
+    return precision == ETICS_MIXED ? etics::radial_keys_impl<float>(posm, N, keys, h.ctx)
+                                    : etics::radial_keys_impl<double>(posm, N, keys, h.ctx);
+}
+
 int etics_leapfrog_step(void* posm, void* vel, void* accpot, int64_t N, double dt, int method,
                         int n_max, int l_max, int precision, double* coeffs_out, void* ws,
                         size_t ws_bytes, void* stream) {

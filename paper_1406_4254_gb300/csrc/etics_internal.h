@@ -20,7 +20,7 @@ int scf_field_f64(const void* posm, int64_t N, int n_max, int l_max, const doubl
 
 // ---- radial sort (etics_sort.cu) -------------------------------------------
 struct SortBuffers {
-    uint32_t *keys_a, *keys_b, *vals_a, *vals_b, *lo;
+    uint32_t *keys_a, *keys_b, *vals_a, *vals_b;
     uint32_t *hist, *status, *counters;
     void* zero_base;
     size_t zero_bytes;
@@ -28,6 +28,9 @@ struct SortBuffers {
 // carve the sort buffers from ws (ws may be null to only compute *total)
 SortBuffers sort_buffers(void* ws, int64_t N, size_t* total);
 int sort_tiles(int64_t N);
+// the 32-bit sort keys alone
+template <typename R>
+int radial_keys_impl(const void* posm, int64_t N, uint32_t* keys, const LaunchCtx& ctx);
 // keys + 4 radix passes + tie fix-up; the order ends in vals_a
 template <typename R>
 int radial_sort_impl(const void* posm, int64_t N, const SortBuffers& b, const LaunchCtx& ctx);

@@ -34,6 +34,13 @@ constexpr int kMexNC = (kMexLB + 1) * (kMexLB + 1);
 
 inline int mex_tiles(int64_t N) { return (int)((N + kMexTile - 1) / kMexTile); }
 
+// shared-memory slot of tile particle i (thread i / kMexP owns particles
+// i..i+kMexP-1): stored particle-major so that a warp reading its threads'
+// k-th particles touches consecutive 16-byte words (no bank conflicts)
+__host__ __device__ constexpr int mex_slot(int i) {
+    return (i % kMexP) * kMexThreads + i / kMexP;
+}
+
 // tile scale exponent: s_t = 2^e with e halfway (in log2) between the first
 // and last radius of the tile (first radius 0 -> use the last)
 template <typename R>
@@ -65,6 +72,9 @@ struct MexParticle {
     }
 };
 
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 // moment of column c of level L: index L*L + c
 template <typename R, int L>
 __device__ __forceinline__ R harm_col(const R* C, const R* S, int c) {
@@ -83,8 +93,10 @@ __device__ __forceinline__ void mex_moments(R (&C)[3][kMexLB + 1], R (&S)[3][kMe
 #pragma unroll
         for (int c = 0; c <= 2 * L; ++c) {
             const R y = harm_col<R, L>(C[s0], S[s0], c);
-            ain[L * L + c] = fma(win, y, ain[L * L + c]);
-            aout[L * L + c] = fma(wout, y, aout[L * L + c]);
+            // separately rounded products: the reverse sweep subtracts exactly
+            // these values again
+            ain[L * L + c] += mul_rn(win, y);
+            aout[L * L + c] += mul_rn(wout, y);
         }
         mex_moments<R, L + 1>(C, S, pt, l_max, win * pt.rho, wout * irho, irho, ain, aout);
     }
@@ -99,7 +111,12 @@ __device__ __forceinline__ void particle_moments(const MexParticle<R>& pt, int l
     mex_moments<R, 0>(C, S, pt, l_max, pt.m, pt.origin ? R(0) : pt.m * irho, irho, ain, aout);
 }
 
-// ---- forward sweep: inner (q) part of the field, then q += own moment ------
+// ---- forward sweep, one particle: inner (q) part of the field, then q += own
+// inner moment.  On entry q is the inner sum over the particles before this
+// one (exclusive).  In tile units (rho = r / s):
+//   Phi_q = -(1/s) sum_l rho^-(l+1) sum_m w_lm q Y
+//   a_q   = (1/s^2) sum_l rho^-(l+2) sum_m w_lm q [G - (2l+1) Y u]
+// with Y, G the unnormalised harmonic and its gradient at the unit vector u.
 template <typename R, int L, bool ACC>
 __device__ __forceinline__ void mex_fwd(R (&C)[3][kMexLB + 1], R (&S)[3][kMexLB + 1],
                                         const MexParticle<R>& pt, int l_max, R win, R rinv,
@@ -113,11 +130,12 @@ __device__ __forceinline__ void mex_fwd(R (&C)[3][kMexLB + 1], R (&S)[3][kMexLB 
 #pragma unroll
             for (int mm = 0; mm <= L; ++mm) {
                 const R w = mex_w<R>(L * (L + 1) / 2 + mm);
-                const R qc = w * q[L * L + (mm == 0 ? 0 : 2 * mm - 1)];
+                const int cc = L * L + (mm == 0 ? 0 : 2 * mm - 1);
+                const R qc = w * q[cc];
                 P = fma(qc, C[s0][mm], P);
                 R qs = R(0);
                 if (mm > 0) {
-                    qs = w * q[L * L + 2 * mm];
+                    qs = w * q[cc + 1];
                     P = fma(qs, S[s0][mm], P);
                 }
                 if (ACC && L >= 1) {
@@ -127,7 +145,6 @@ __device__ __forceinline__ void mex_fwd(R (&C)[3][kMexLB + 1], R (&S)[3][kMexLB 
                     if (mm > 0) { vx = fma(qs, gs[0], vx); vy = fma(qs, gs[1], vy); vz = fma(qs, gs[2], vz); }
                 }
             }
-            // potential  -rho^-(l+1) P ;  a = rho^-(l+2) (V - (2l+1) P u)
             pot = fma(rinv, P, pot);
             if (ACC) {
                 const R f = rinv * irho;
@@ -139,12 +156,14 @@ __device__ __forceinline__ void mex_fwd(R (&C)[3][kMexLB + 1], R (&S)[3][kMexLB 
         }
 #pragma unroll
         for (int c = 0; c <= 2 * L; ++c)
-            q[L * L + c] = fma(win, harm_col<R, L>(C[s0], S[s0], c), q[L * L + c]);
+            q[L * L + c] += mul_rn(win, harm_col<R, L>(C[s0], S[s0], c));
         mex_fwd<R, L + 1, ACC>(C, S, pt, l_max, win * pt.rho, rinv * irho, irho, q, pot, ax, ay, az);
     }
 }
 
-// ---- reverse sweep: outer (p) part of the field, then p += own moment ------
+// ---- reverse sweep, one particle: outer (p) part of the field, then p += own
+// outer moment.  On entry p is the outer sum over the particles after this one:
+//   Phi_p = -(1/s) sum_l rho^l sum_m w_lm p Y,   a_p = (1/s^2) sum_l rho^(l-1) sum_m w_lm p G
 template <typename R, int L, bool ACC>
 __device__ __forceinline__ void mex_rev(R (&C)[3][kMexLB + 1], R (&S)[3][kMexLB + 1],
                                         const MexParticle<R>& pt, int l_max, R wout, R rl,
@@ -158,11 +177,12 @@ __device__ __forceinline__ void mex_rev(R (&C)[3][kMexLB + 1], R (&S)[3][kMexLB 
 #pragma unroll
         for (int mm = 0; mm <= L; ++mm) {
             const R w = mex_w<R>(L * (L + 1) / 2 + mm);
-            const R pc = w * p[L * L + (mm == 0 ? 0 : 2 * mm - 1)];
+            const int cc = L * L + (mm == 0 ? 0 : 2 * mm - 1);
+            const R pc = w * p[cc];
             P = fma(pc, C[s0][mm], P);
             R ps = R(0);
             if (mm > 0) {
-                ps = w * p[L * L + 2 * mm];
+                ps = w * p[cc + 1];
                 P = fma(ps, S[s0][mm], P);
             }
             if (ACC && L >= 1) {
@@ -172,7 +192,6 @@ __device__ __forceinline__ void mex_rev(R (&C)[3][kMexLB + 1], R (&S)[3][kMexLB 
                 if (mm > 0) { vx = fma(ps, gs[0], vx); vy = fma(ps, gs[1], vy); vz = fma(ps, gs[2], vz); }
             }
         }
-        // potential -rho^l P;  a = -grad: rho^(l-1) V (l >= 1)
         pot = fma(rl, P, pot);
         if (ACC && L >= 1) {
             ax = fma(rlm1, vx, ax);
@@ -181,9 +200,9 @@ __device__ __forceinline__ void mex_rev(R (&C)[3][kMexLB + 1], R (&S)[3][kMexLB 
         }
 #pragma unroll
         for (int c = 0; c <= 2 * L; ++c)
-            p[L * L + c] = fma(wout, harm_col<R, L>(C[s0], S[s0], c), p[L * L + c]);
-        mex_rev<R, L + 1, ACC>(C, S, pt, l_max, wout * irho, rl * pt.rho, rl, irho, p, pot, ax, ay,
-                               az);
+            p[L * L + c] += mul_rn(wout, harm_col<R, L>(C[s0], S[s0], c));
+        mex_rev<R, L + 1, ACC>(C, S, pt, l_max, wout * irho, rl * pt.rho, rl, irho, p, pot, ax,
+                               ay, az);
     }
 }
 
@@ -195,38 +214,47 @@ __global__ void __launch_bounds__(kMexThreads)
 mex_pass1_kernel(const Vec4<R>* __restrict__ posm, const uint32_t* __restrict__ perm, int64_t N,
                  int l_max, Vec4<R>* __restrict__ sorted, double* __restrict__ tile_agg,
                  unsigned* err) {
-    __shared__ R s_r[2];
+    __shared__ Vec4<R> s_pt[kMexTile];
     __shared__ R s_red[kMexThreads / 32][2 * kMexNC];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t base = (int64_t)blockIdx.x * kMexTile;
-    const int64_t last = (base + kMexTile < N ? base + kMexTile : N) - 1;
-    Vec4<R> pp[kMexP];
+    const int64_t rem = N - base;
+    const int nt = (int)(rem < kMexTile ? rem : kMexTile);
+    // gather in radial order: coalesced index loads, independent particle loads
+    uint32_t idx[kMexP];
 #pragma unroll
-    for (int k = 0; k < kMexP; ++k) {
-        const int64_t i = base + (int64_t)tid * kMexP + k;
-        if (i < N) {
-            pp[k] = ld4(posm + perm[i]);
-            if (!finite4(pp[k].x, pp[k].y, pp[k].z, pp[k].w)) {
+    for (int j = 0; j < kMexP; ++j) {
+        const int i = tid + j * kMexThreads;
+        idx[j] = i < nt ? perm[base + i] : 0u;
+    }
+#pragma unroll
+    for (int j = 0; j < kMexP; ++j) {
+        const int i = tid + j * kMexThreads;
+        Vec4<R> v = mk4<R>(R(0), R(0), R(0), R(0));
+        if (i < nt) {
+            v = ld4(posm + idx[j]);
+            if (!finite4(v.x, v.y, v.z, v.w)) {
                 report(err, ETICS_ERR_NONFINITE);
-                pp[k] = mk4<R>(R(0), R(0), R(0), R(0));
+                v = mk4<R>(R(0), R(0), R(0), R(0));
             }
-            st4(sorted + i, pp[k]);
-            if (i == base) s_r[0] = radius<R>(pp[k].x, pp[k].y, pp[k].z);
-            if (i == last) s_r[1] = radius<R>(pp[k].x, pp[k].y, pp[k].z);
-        } else {
-            pp[k] = mk4<R>(R(0), R(0), R(0), R(0));
+            st4(sorted + base + i, v);
         }
+        st4(&s_pt[mex_slot(i)], v);
     }
     __syncthreads();
-    const int e = tile_exponent<R>(s_r[0], s_r[1]);
+    int e;
+    {
+        const Vec4<R> a = s_pt[mex_slot(0)], b = s_pt[mex_slot(nt - 1)];
+        e = tile_exponent<R>(radius<R>(a.x, a.y, a.z), radius<R>(b.x, b.y, b.z));
+    }
     const R scale = ldexp(R(1), -e);
     R ain[kMexNC], aout[kMexNC];
 #pragma unroll
     for (int c = 0; c < kMexNC; ++c) { ain[c] = R(0); aout[c] = R(0); }
-#pragma unroll
+#pragma unroll 1
     for (int k = 0; k < kMexP; ++k) {
         MexParticle<R> pt;
-        pt.init(pp[k], scale);
+        pt.init(s_pt[k * kMexThreads + tid], scale);
         particle_moments<R>(pt, l_max, ain, aout);
     }
 #pragma unroll
@@ -299,18 +327,22 @@ mex_pass2_kernel(const Vec4<R>* __restrict__ sorted, const uint32_t* __restrict_
                  int l_max, const double* __restrict__ carry, Vec4<R>* __restrict__ out,
                  int out_mask, unsigned* err) {
     constexpr int NW = kMexThreads / 32;
+    __shared__ Vec4<R> s_pt[kMexTile];
+    __shared__ Vec4<R> s_f[kMexTile];   // inner part of each particle's field
     __shared__ R s_q0[kMexNC], s_p0[kMexNC];
     __shared__ R s_wq[NW][kMexNC], s_wp[NW][kMexNC];
-    __shared__ int s_e;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t base = (int64_t)blockIdx.x * kMexTile;
-    const int64_t last = (base + kMexTile < N ? base + kMexTile : N) - 1;
-    if (tid == 0) {
-        const Vec4<R> a = ld4(sorted + base), b = ld4(sorted + last);
-        s_e = tile_exponent<R>(radius<R>(a.x, a.y, a.z), radius<R>(b.x, b.y, b.z));
-    }
+    const int64_t rem = N - base;
+    const int nt = (int)(rem < kMexTile ? rem : kMexTile);
+    for (int i = tid; i < kMexTile; i += kMexThreads)
+        st4(&s_pt[mex_slot(i)], i < nt ? ld4(sorted + base + i) : mk4<R>(R(0), R(0), R(0), R(0)));
     __syncthreads();
-    const int e = s_e;
+    int e;
+    {
+        const Vec4<R> a = s_pt[mex_slot(0)], b = s_pt[mex_slot(nt - 1)];
+        e = tile_exponent<R>(radius<R>(a.x, a.y, a.z), radius<R>(b.x, b.y, b.z));
+    }
     const R scale = ldexp(R(1), -e);
     for (int c = tid; c < 2 * kMexNC; c += kMexThreads) {
         const int cc = c % kMexNC;
@@ -320,23 +352,18 @@ mex_pass2_kernel(const Vec4<R>* __restrict__ sorted, const uint32_t* __restrict_
         if (c < kMexNC) s_q0[cc] = (R)ldexp(v, -l * e);
         else s_p0[cc] = (R)ldexp(v, (l + 1) * e);
     }
-    Vec4<R> pp[kMexP];
-#pragma unroll
-    for (int k = 0; k < kMexP; ++k) {
-        const int64_t i = base + (int64_t)tid * kMexP + k;
-        pp[k] = (i < N) ? ld4(sorted + i) : mk4<R>(R(0), R(0), R(0), R(0));
-    }
-    // thread sums of the inner and outer moments
+    // thread sums of the inner and outer moments of its kMexP particles
     R a[kMexNC], b[kMexNC];
 #pragma unroll
     for (int c = 0; c < kMexNC; ++c) { a[c] = R(0); b[c] = R(0); }
-#pragma unroll
+#pragma unroll 1
     for (int k = 0; k < kMexP; ++k) {
         MexParticle<R> pt;
-        pt.init(pp[k], scale);
+        pt.init(s_pt[k * kMexThreads + tid], scale);
         particle_moments<R>(pt, l_max, a, b);
     }
-    // warp scans: exclusive prefix of a (forward), exclusive suffix of b (reverse)
+    // inner sums: exclusive prefix before this thread; outer sums: exclusive
+    // suffix after it (a true suffix sum, never total minus prefix)
 #pragma unroll
     for (int c = 0; c < kMexNC; ++c) {
         R x = a[c], y = b[c];
@@ -349,8 +376,8 @@ mex_pass2_kernel(const Vec4<R>* __restrict__ sorted, const uint32_t* __restrict_
         }
         if (lane == 31) s_wq[warp][c] = x;
         if (lane == 0) s_wp[warp][c] = y;
-        R ex = __shfl_up_sync(0xffffffffu, x, 1);
-        R ey = __shfl_down_sync(0xffffffffu, y, 1);
+        const R ex = __shfl_up_sync(0xffffffffu, x, 1);
+        const R ey = __shfl_down_sync(0xffffffffu, y, 1);
         a[c] = (lane == 0) ? R(0) : ex;
         b[c] = (lane == 31) ? R(0) : ey;
     }
@@ -363,39 +390,37 @@ mex_pass2_kernel(const Vec4<R>* __restrict__ sorted, const uint32_t* __restrict_
         a[c] = q0 + a[c];
         b[c] = p0 + b[c];
     }
-    // forward sweep (inner part of the field), reverse sweep (outer part)
-    R fpot[kMexP], fax[kMexP], fay[kMexP], faz[kMexP];
-#pragma unroll
+    // forward sweep (inner part of the field, kept in shared memory), then the
+    // reverse sweep (outer part) which completes and scatters each particle
+#pragma unroll 1
     for (int k = 0; k < kMexP; ++k) {
         MexParticle<R> pt;
-        pt.init(pp[k], scale);
+        pt.init(s_pt[k * kMexThreads + tid], scale);
         const R irho = pt.origin ? R(0) : R(1) / pt.rho;
         R C[3][kMexLB + 1], S[3][kMexLB + 1];
-        fpot[k] = fax[k] = fay[k] = faz[k] = R(0);
-        mex_fwd<R, 0, ACC>(C, S, pt, l_max, pt.m, irho, irho, a, fpot[k], fax[k], fay[k], faz[k]);
+        R pot = R(0), ax = R(0), ay = R(0), az = R(0);
+        mex_fwd<R, 0, ACC>(C, S, pt, l_max, pt.m, irho, irho, a, pot, ax, ay, az);
+        st4(&s_f[k * kMexThreads + tid], mk4<R>(ax, ay, az, pot));
     }
-#pragma unroll
+    const R s1 = scale, s2 = scale * scale;
+#pragma unroll 1
     for (int k = kMexP - 1; k >= 0; --k) {
         MexParticle<R> pt;
-        pt.init(pp[k], scale);
+        pt.init(s_pt[k * kMexThreads + tid], scale);
         const R irho = pt.origin ? R(0) : R(1) / pt.rho;
         R C[3][kMexLB + 1], S[3][kMexLB + 1];
+        const Vec4<R> f = s_f[k * kMexThreads + tid];
+        R pot = f.w, ax = f.x, ay = f.y, az = f.z;
         const R wout = pt.origin ? R(0) : pt.m * irho;
-        mex_rev<R, 0, ACC>(C, S, pt, l_max, wout, R(1), R(0), irho, b, fpot[k], fax[k], fay[k],
-                           faz[k]);
-    }
-    // back to physical units: Phi = -F / s, a = grad-part / s^2; scatter
-    const R s1 = scale, s2 = scale * scale;
-#pragma unroll
-    for (int k = 0; k < kMexP; ++k) {
+        mex_rev<R, 0, ACC>(C, S, pt, l_max, wout, R(1), R(0), irho, b, pot, ax, ay, az);
         const int64_t i = base + (int64_t)tid * kMexP + k;
         if (i < N) {
-            const R pot = (out_mask & ETICS_OUT_POT) ? -fpot[k] * s1 : R(0);
-            const R ax = ACC ? fax[k] * s2 : R(0);
-            const R ay = ACC ? fay[k] * s2 : R(0);
-            const R az = ACC ? faz[k] * s2 : R(0);
-            if (!finite4(ax, ay, az, pot)) report(err, ETICS_ERR_NONFINITE);
-            st4(out + perm[i], mk4<R>(ax, ay, az, pot));
+            const R potv = (out_mask & ETICS_OUT_POT) ? -pot * s1 : R(0);
+            const R fx = ACC ? ax * s2 : R(0);
+            const R fy = ACC ? ay * s2 : R(0);
+            const R fz = ACC ? az * s2 : R(0);
+            if (!finite4(fx, fy, fz, potv)) report(err, ETICS_ERR_NONFINITE);
+            st4(out + perm[i], mk4<R>(fx, fy, fz, potv));
         }
     }
 }

@@ -47,6 +47,7 @@ struct ScfCoeffParams {
     int T;            // particles per tile (multiple of 4)
     int W, G;         // register-tile items and particle groups per item
     int ntiles;
+    int l_split;      // radial levels [0, l_split) by the first half of the block
     double* partial;  // [gridDim.x][W*NR*4]
     unsigned* err;
 };
@@ -89,8 +90,35 @@ __device__ __forceinline__ void angular_levels(R (&C)[3][LMU + 1], R (&S)[3][LMU
     }
 }
 
+// phase 1, radial part: Rs[l][n][k] = m phi_nl(r_k) = w_l C_n^(2l+3/2)(xi) for
+// levels l in [l_begin, l_end] (compile-time recursion over the level, n
+// unrolled to NR so the recursion constants are immediates).  Rows n > n_max
+// stay zero.  w_l = -m (1+r)^-1 (r/(1+r)^2)^l.
+template <typename R, int NR, int L, int LMU>
+__device__ __forceinline__ void radial_levels(R* Rs, int T, int k, int n_max, int l_begin,
+                                              int l_end, R w, R st, R xi) {
+    if constexpr (L <= LMU) {
+        if (L > l_end) return;
+        if (L >= l_begin) {
+            R* row = Rs + (size_t)L * NR * T + k;
+            R cm1 = R(0), c = R(1);
+            row[0] = w;
+#pragma unroll
+            for (int n = 1; n < NR; ++n) {
+                if (n <= n_max) {
+                    const R cn = geg_a<R>(L, n) * xi * c - geg_b<R>(L, n) * cm1;
+                    cm1 = c;
+                    c = cn;
+                    row[(size_t)n * T] = w * c;
+                }
+            }
+        }
+        radial_levels<R, NR, L + 1, LMU>(Rs, T, k, n_max, l_begin, l_end, w * st, st, xi);
+    }
+}
+
 template <typename R, int NR, int LMU>
-__global__ void __launch_bounds__(ScfCfg<R>::kThreads)
+__global__ void __launch_bounds__(ScfCfg<R>::kThreads, 2)
 scf_coeff_kernel(ScfCoeffParams p) {
     constexpr int TH = ScfCfg<R>::kThreads;
     using V4 = Vec4<R>;
@@ -138,14 +166,14 @@ scf_coeff_kernel(ScfCoeffParams p) {
             for (int n = 0; n < NR; ++n)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    red[((size_t)(item * NR + n) * 4 + j) * p.G + g] = acc[n][j];
+                    red[(size_t)g * nout + (item * NR + n) * 4 + j] = acc[n][j];
                     acc[n][j] = R(0);
                 }
         }
         __syncthreads();
         for (int o = tid; o < nout; o += TH) {
             R s = R(0);
-            for (int gg = 0; gg < p.G; ++gg) s += red[(size_t)o * p.G + gg];
+            for (int gg = 0; gg < p.G; ++gg) s += red[(size_t)gg * nout + o];
             accd[o] += (double)s;
         }
         __syncthreads();
@@ -153,45 +181,41 @@ scf_coeff_kernel(ScfCoeffParams p) {
         __syncthreads();
     };
 
+    // this thread's particle of the current tile (prefetched one tile ahead)
+    const int kp = tid < T ? tid : tid - T;
+    auto load_particle = [&](int tile) -> V4 {
+        const int64_t gi = (int64_t)tile * T + kp;
+        if (tid < 2 * T && tile < p.ntiles && gi < p.N) return ld4(posm + gi);
+        return mk4<R>(R(0), R(0), R(0), R(0));
+    };
+    V4 cur = load_particle(blockIdx.x);
     int since_flush = 0;
     for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
         // ---- phase 1: basis functions of the tile's particles -------------
         if (tid < 2 * T) {
-            const int k = tid < T ? tid : tid - T;
-            const int64_t gi = (int64_t)tile * T + k;
+            const int k = kp;
             R x = R(0), y = R(0), z = R(0), m = R(0);
-            if (gi < p.N) {
-                V4 v = ld4(posm + gi);
-                if (finite4(v.x, v.y, v.z, v.w)) { x = v.x; y = v.y; z = v.z; m = v.w; }
-                else if (tid < T) report(p.err, ETICS_ERR_NONFINITE);
-            }
+            if (finite4(cur.x, cur.y, cur.z, cur.w)) { x = cur.x; y = cur.y; z = cur.z; m = cur.w; }
+            else if (tid < T) report(p.err, ETICS_ERR_NONFINITE);
             const R r = sqrt(x * x + y * y + z * z);
+            const R t = R(1) / (R(1) + r);
+            const R st = r * t * t;
+            const R xi = R(1) - R(2) * t;
             if (tid < T) {
-                // radial: R[l][n][k] = m phi_nl(r) = m pre_l(r) C_n^(2l+3/2)(xi)
-                const R t = R(1) / (R(1) + r);
-                const R st = r * t * t;
-                const R xi = R(1) - R(2) * t;
-                R w = -m * t;
-                for (int l = 0; l < L1; ++l) {
-                    R cm1 = R(0), c = R(1);
-                    R* row = Rs + (size_t)l * NR * T + k;
-                    row[0] = w;
-                    for (int n = 1; n <= p.n_max; ++n) {
-                        const R cn = geg_a<R>(l, n) * xi * c - geg_b<R>(l, n) * cm1;
-                        cm1 = c;
-                        c = cn;
-                        row[(size_t)n * T] = w * c;
-                    }
-                    w *= st;
-                }
+                // radial levels [0, l_split)
+                radial_levels<R, NR, 0, LMU>(Rs, T, k, p.n_max, 0, p.l_split - 1, -m * t, st, xi);
             } else {
+                // angular basis of every level, then radial levels [l_split, l_max]
                 const R inv = r > R(0) ? R(1) / r : R(0);
                 const R ux = x * inv, uy = y * inv, uz = z * inv;
                 const R uu = ux * ux + uy * uy + uz * uz;
                 R C[3][LMU + 1], S[3][LMU + 1];
                 angular_levels<R, 0, LMU>(C, S, ux, uy, uz, uu, p.l_max, Ys, T, k);
+                radial_levels<R, NR, 0, LMU>(Rs, T, k, p.n_max, p.l_split, p.l_max, -m * t, st,
+                                             xi);
             }
         }
+        cur = load_particle(tile + gridDim.x);
         __syncthreads();
         // ---- phase 2: register-tiled contraction over the tile -------------
         if (active) {
@@ -257,7 +281,10 @@ static __global__ void scf_finalize_kernel(const double* __restrict__ partial, i
 // ---------------------------------------------------------------------------
 // field pass
 // ---------------------------------------------------------------------------
-template <typename R, int LM, bool ACC>
+// NM1 > 0: specialised for n_max + 1 == NM1 and l_max == LM (n loop unrolled,
+// coefficient row stride and recursion constants known at compile time);
+// NM1 == 0: generic, n_max and l_max <= LM at run time.
+template <typename R, int LM, bool ACC, int NM1>
 struct FieldEval {
     using V4 = Vec4<R>;
     R C[3][LM + 1], S[3][LM + 1];
@@ -269,7 +296,7 @@ struct FieldEval {
     template <int L>
     __device__ __forceinline__ void level() {
         if constexpr (L <= LM) {
-            if (L > l_max) return;
+            if (NM1 == 0 && L > l_max) return;
             constexpr int s0 = L % 3, s1 = (L + 2) % 3, s2 = (L + 1) % 3;
             harm_level<R, L>(C[s1], S[s1], C[s2], S[s2], ux, uy, uz, uu, C[s0], S[s0]);
             constexpr int NC = 2 * L + 1;
@@ -279,8 +306,12 @@ struct FieldEval {
 #pragma unroll
             for (int c = 0; c < NC; ++c) { A[c] = R(0); B[c] = R(0); }
             R cm1 = R(0), cn = R(1), dm1 = R(0), dn = R(0);
+            constexpr int kStride = NM1 > 0 ? col_offset_c(LM + 1) : 0;
+            const int stride = NM1 > 0 ? kStride : ncols;
+            const int nlim = NM1 > 0 ? NM1 - 1 : n_max;
             const R* row = cs + CO;
-            for (int n = 0; n <= n_max; ++n, row += ncols) {
+#pragma unroll (NM1 > 0 ? NM1 : 1)
+            for (int n = 0; n <= nlim; ++n, row += stride) {
                 if (n > 0) {
                     const R a = geg_a<R>(L, n), b = geg_b<R>(L, n);
                     const R cnew = a * xi * cn - b * cm1;
@@ -350,8 +381,8 @@ struct FieldEval {
     }
 };
 
-template <typename R, int LM, bool ACC>
-__global__ void __launch_bounds__(kFieldThreads)
+template <typename R, int LM, bool ACC, int NM1>
+__global__ void __launch_bounds__(kFieldThreads, 2)
 scf_field_kernel(const Vec4<R>* __restrict__ posm, int64_t N, int n_max, int l_max,
                  const double* __restrict__ coeffs, Vec4<R>* __restrict__ out, int out_mask,
                  unsigned* err) {
@@ -376,7 +407,7 @@ scf_field_kernel(const Vec4<R>* __restrict__ posm, int64_t N, int n_max, int l_m
          i += (int64_t)gridDim.x * blockDim.x) {
         const Vec4<R> pv = ld4(posm + i);
         if (!finite4(pv.x, pv.y, pv.z, pv.w)) report(err, ETICS_ERR_NONFINITE);
-        FieldEval<R, LM, ACC> f;
+        FieldEval<R, LM, ACC, NM1> f;
         const R r = sqrt(pv.x * pv.x + pv.y * pv.y + pv.z * pv.z);
         const R inv = r > R(0) ? R(1) / r : R(0);
         f.ux = pv.x * inv; f.uy = pv.y * inv; f.uz = pv.z * inv;
@@ -479,6 +510,19 @@ inline int scf_coeffs_launch(const void* posm, int64_t N, int n_max, int l_max, 
     p.W = W;
     p.G = G;
     p.ntiles = ntiles;
+    {
+        // balance phase 1: radial levels cost ~(n_max+1) each, the angular
+        // basis ~(l_max+1)^2; give the angular half the top radial levels
+        const double rad = n_max + 1.0, ang = 0.8 * (l_max + 1.0) * (l_max + 1.0);
+        int best = l_max + 1;
+        double best_cost = 1e30;
+        for (int ls = 0; ls <= l_max + 1; ++ls) {
+            const double a = rad * ls, b = ang + rad * (l_max + 1 - ls);
+            const double c = a > b ? a : b;
+            if (c < best_cost) { best_cost = c; best = ls; }
+        }
+        p.l_split = best;
+    }
     p.partial = reinterpret_cast<double*>(ws);
     p.err = ctx.err;
     int nblocks = 0;
@@ -506,7 +550,7 @@ inline int scf_coeffs_launch(const void* posm, int64_t N, int n_max, int l_max, 
     return ETICS_OK;
 }
 
-template <typename R, int LM>
+template <typename R, int LM, int NM1 = 0>
 inline int launch_field_lm(const void* posm, int64_t N, int n_max, int l_max,
                            const double* coeffs, void* out, int out_mask, const LaunchCtx& ctx) {
     const size_t smem = (size_t)(n_max + 1) * col_total(l_max) * sizeof(R);
@@ -517,14 +561,14 @@ inline int launch_field_lm(const void* posm, int64_t N, int n_max, int l_max,
     const Vec4<R>* pp = reinterpret_cast<const Vec4<R>*>(posm);
     Vec4<R>* op = reinterpret_cast<Vec4<R>*>(out);
     if (out_mask & ETICS_OUT_ACC) {
-        auto k = scf_field_kernel<R, LM, true>;
+        auto k = scf_field_kernel<R, LM, true, NM1>;
         if (smem > 48 * 1024 &&
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
             return ETICS_ERR_CUDA;
         k<<<grid, kFieldThreads, smem, ctx.stream>>>(pp, N, n_max, l_max, coeffs, op, out_mask,
                                                      ctx.err);
     } else {
-        auto k = scf_field_kernel<R, LM, false>;
+        auto k = scf_field_kernel<R, LM, false, NM1>;
         if (smem > 48 * 1024 &&
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
             return ETICS_ERR_CUDA;
@@ -540,6 +584,11 @@ template <typename R>
 inline int scf_field_launch(const void* posm, int64_t N, int n_max, int l_max,
                             const double* coeffs, void* out, int out_mask, const LaunchCtx& ctx) {
     if (N == 0) return ETICS_OK;
+    // specialised instantiations for the configurations of the paper's tests
+    if (n_max == 10 && l_max == 6)
+        return launch_field_lm<R, 6, 11>(posm, N, n_max, l_max, coeffs, out, out_mask, ctx);
+    if (n_max == 14 && l_max == 8)
+        return launch_field_lm<R, 8, 15>(posm, N, n_max, l_max, coeffs, out, out_mask, ctx);
     if (l_max <= 2) return launch_field_lm<R, 2>(posm, N, n_max, l_max, coeffs, out, out_mask, ctx);
     if (l_max <= 4) return launch_field_lm<R, 4>(posm, N, n_max, l_max, coeffs, out, out_mask, ctx);
     if (l_max <= 6) return launch_field_lm<R, 6>(posm, N, n_max, l_max, coeffs, out, out_mask, ctx);

@@ -16,6 +16,7 @@ namespace etics {
 constexpr int kSortThreads = 256;
 constexpr int kSortKpt = 16;
 constexpr int kSortTile = kSortThreads * kSortKpt;   // 4096 keys per tile
+constexpr int kLookbackWindow = 32;
 constexpr uint32_t kCountMask = (1u << 30) - 1;
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagInc = 2u << 30;
@@ -29,37 +30,126 @@ __device__ __forceinline__ double r2_fp64(double x, double y, double z) {
     return __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z));
 }
 
+// High 32 bits of the FP64 bit pattern of r^2 (the sort key; positive doubles
+// order like their bit patterns).
+//
+// FP32 particles: every square is exact in FP64, so fl64(fl64(x*x+y*y)+z*z)
+// differs from the exact sum S by at most 2 FP64 ulps.  S is evaluated as an
+// FP32 pair (hi, lo) with error ~2^-45 |S| (exact products by FMA, TwoSum),
+// and the key is read off the pair: the top 20 mantissa bits of hi, minus one
+// when lo < 0 borrows across a bucket boundary (the low 3 mantissa bits of hi
+// are zero).  Only when S lies within 2^-40 |S| of a bucket boundary is the
+// key recomputed in FP64, so the result always equals the FP64 evaluation.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ uint32_t key_from_fp64(double r2) {
+    return (uint32_t)((uint64_t)__double_as_longlong(r2) >> 32);
+}
+
+__device__ __forceinline__ uint32_t r2_key(float x, float y, float z) {
+    const float hx = x * x, lx = fmaf(x, x, -hx);
+    const float hy = y * y, ly = fmaf(y, y, -hy);
+    const float hz = z * z, lz = fmaf(z, z, -hz);
+    float s1, e1, s2, e2;
+    two_sum(hx, hy, s1, e1);
+    two_sum(s1, hz, s2, e2);
+    const float low = ((lx + ly) + lz) + (e1 + e2);
+    const float hi = s2 + low;                  // fast two-sum: |s2| >= |low|
+    const float lo = low - (hi - s2);
+    const uint32_t hb = __float_as_uint(hi);
+    const uint32_t exp8 = hb >> 23, frac = hb & 0x7fffffu;
+    // tiny (r^2 < 2^-63), non-finite or overflowing sums take the FP64 route
+    bool exact_needed = exp8 < 64u || exp8 == 255u;
+    uint32_t key = 0;
+    if (!exact_needed) {
+        key = ((exp8 + 896u) << 20) | (frac >> 3);   // FP64 exponent field = exp8 - 127 + 1023
+        if ((frac & 7u) == 0u) {
+            if (fabsf(lo) <= hi * 0x1p-40f) exact_needed = true;   // too close to call
+            else if (lo < 0.0f) key -= 1u;                        // borrow below the boundary
+        }
+    }
+    if (exact_needed) {
+        const double dx = x, dy = y, dz = z;
+        key = key_from_fp64(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
+                                      __dmul_rn(dz, dz)));
+    }
+    return key;
+}
+__device__ __forceinline__ uint32_t r2_key(double x, double y, double z) {
+    return key_from_fp64(r2_fp64(x, y, z));
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256)
 keygen_kernel(const Vec4<R>* __restrict__ posm, int64_t N, uint32_t* __restrict__ key,
-              uint32_t* __restrict__ lo, uint32_t* __restrict__ val, uint32_t* __restrict__ hist,
-              unsigned* err) {
-    __shared__ uint32_t sh[4 * 256];
-    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) sh[i] = 0;
+              uint32_t* __restrict__ val, uint32_t* __restrict__ hist, unsigned* err) {
+    // one private copy of the 4 digit histograms per warp (less atomic contention)
+    __shared__ uint32_t sh[8][4 * 256];
+    const int warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < 8 * 4 * 256; i += blockDim.x) (&sh[0][0])[i] = 0;
     __syncthreads();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
         const Vec4<R> v = ld4(posm + i);
-        uint64_t bits;
+        uint32_t hi;
         if (finite4(v.x, v.y, v.z, v.w)) {
-            bits = (uint64_t)__double_as_longlong(r2_fp64((double)v.x, (double)v.y, (double)v.z));
+            hi = r2_key(v.x, v.y, v.z);
         } else {
             report(err, ETICS_ERR_NONFINITE);
-            bits = ~0ull;
+            hi = 0xffffffffu;
         }
-        const uint32_t hi = (uint32_t)(bits >> 32);
         key[i] = hi;
-        lo[i] = (uint32_t)bits;
         val[i] = (uint32_t)i;
-        atomicAdd(&sh[hi & 255], 1u);
-        atomicAdd(&sh[256 + ((hi >> 8) & 255)], 1u);
-        atomicAdd(&sh[512 + ((hi >> 16) & 255)], 1u);
-        atomicAdd(&sh[768 + (hi >> 24)], 1u);
+        atomicAdd(&sh[warp][hi & 255], 1u);
+        atomicAdd(&sh[warp][256 + ((hi >> 8) & 255)], 1u);
+        atomicAdd(&sh[warp][512 + ((hi >> 16) & 255)], 1u);
+        // the top byte (sign + high exponent bits) takes very few values:
+        // aggregate equal digits within the warp before the atomic
+        const uint32_t d3 = hi >> 24;
+        const unsigned same = __match_any_sync(__activemask(), d3);
+        if ((same & ((1u << (threadIdx.x & 31)) - 1u)) == 0u)
+            atomicAdd(&sh[warp][768 + d3], (uint32_t)__popc(same));
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x)
-        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) {
+        uint32_t t = 0;
+        for (int w = 0; w < 8; ++w) t += sh[w][i];
+        if (t) atomicAdd(&hist[i], t);
+    }
 }
+
+template <typename R>
+__global__ void radial_keys_kernel(const Vec4<R>* __restrict__ posm, int64_t N,
+                                   uint32_t* __restrict__ keys, unsigned* err) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const Vec4<R> v = ld4(posm + i);
+        if (finite4(v.x, v.y, v.z, v.w)) {
+            keys[i] = r2_key(v.x, v.y, v.z);
+        } else {
+            report(err, ETICS_ERR_NONFINITE);
+            keys[i] = 0xffffffffu;
+        }
+    }
+}
+
+template <typename R>
+int radial_keys_impl(const void* posm, int64_t N, uint32_t* keys, const LaunchCtx& ctx) {
+    if (N == 0) return ETICS_OK;
+    int g = (int)((N + 255) / 256);
+    if (g > ctx.num_sms * 8) g = ctx.num_sms * 8;
+    radial_keys_kernel<R><<<g, 256, 0, ctx.stream>>>(reinterpret_cast<const Vec4<R>*>(posm), N,
+                                                      keys, ctx.err);
+    if (cudaGetLastError()) return ETICS_ERR_CUDA;
+    ++*ctx.launches;
+    return ETICS_OK;
+}
+template int radial_keys_impl<float>(const void*, int64_t, uint32_t*, const LaunchCtx&);
+template int radial_keys_impl<double>(const void*, int64_t, uint32_t*, const LaunchCtx&);
 
 // exclusive scan over the 256 threads of a block (one value per thread)
 __device__ __forceinline__ uint32_t block_excl_scan256(uint32_t v, uint32_t* s_warp) {
@@ -85,7 +175,7 @@ __device__ __forceinline__ void st_volatile(uint32_t* p, uint32_t v) {
     *reinterpret_cast<volatile uint32_t*>(p) = v;
 }
 
-__global__ void __launch_bounds__(kSortThreads)
+__global__ void __launch_bounds__(kSortThreads, 2)
 onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                 uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
                 const uint32_t* __restrict__ hist, uint32_t* status, uint32_t* counter, int shift,
@@ -142,22 +232,47 @@ onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
     // decoupled lookback over earlier tiles for this digit
     uint32_t* st = status + (size_t)tile * 256;
     uint32_t excl = 0;
-    if (tile == 0) {
+    const uint32_t gcount = hist[dig];
+    if (tile == 0 || gcount == 0u) {
+        // tile 0, or a digit no key has (nobody looks it up)
         st_volatile(st + dig, kFlagInc | count);
     } else {
         st_volatile(st + dig, kFlagAgg | count);
+        // look back over a window of predecessors at once (independent loads),
+        // summing aggregates until an inclusive prefix is found; tile 0 always
+        // publishes an inclusive prefix, so the walk ends
         int64_t t = (int64_t)tile - 1;
         int spins = 0;
         while (t >= 0) {
-            const uint32_t sv = ld_volatile(status + (size_t)t * 256 + dig);
-            if ((sv & ~kCountMask) == 0u) {
+            uint32_t w[kLookbackWindow];
+#pragma unroll
+            for (int j = 0; j < kLookbackWindow; ++j)
+                w[j] = (t - j >= 0) ? ld_volatile(status + (size_t)(t - j) * 256 + dig) : 0u;
+            // consume the window in order up to the first inclusive prefix or
+            // the first predecessor that has not published yet (slots beyond
+            // tile 0 read as unpublished, and tile 0 is always inclusive)
+            int used;
+            bool done = false;
+            int first_inc = kLookbackWindow, first_wait = kLookbackWindow;
+#pragma unroll
+            for (int j = kLookbackWindow - 1; j >= 0; --j) {
+                const uint32_t flag = w[j] & ~kCountMask;
+                if (flag == 0u) first_wait = j;
+                if (flag == kFlagInc) first_inc = j;
+            }
+            if (first_inc < first_wait) { used = first_inc + 1; done = true; }
+            else used = first_wait;
+            if (used > t + 1) used = (int)(t + 1);
+#pragma unroll
+            for (int j = 0; j < kLookbackWindow; ++j)
+                if (j < used) excl += w[j] & kCountMask;
+            if (done) break;
+            t -= used;
+            const bool wait = used < kLookbackWindow && t >= 0;
+            if (wait) {
                 if (++spins > kSpinLimit) { report(err, ETICS_ERR_TIMEOUT); break; }
                 __nanosleep(32);
-                continue;
             }
-            excl += sv & kCountMask;
-            if ((sv & ~kCountMask) == kFlagInc) break;
-            --t;
         }
         st_volatile(st + dig, kFlagInc | (excl + count));
     }
@@ -187,10 +302,21 @@ onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
     }
 }
 
-// Runs of equal high words: order by (low word, index).  The run's first
-// element owns it; runs longer than kMaxTieRun are reported as unsupported.
-__global__ void tie_fixup_kernel(const uint32_t* __restrict__ key, const uint32_t* __restrict__ lo,
+// Runs of equal high words: order by (low word of the FP64 r^2, index).  The
+// run's first element owns it; the low words are evaluated here, in FP64, for
+// the run members only.  Runs longer than kMaxTieRun are reported as
+// unsupported (left in index order).
+template <typename R>
+__device__ __forceinline__ uint32_t r2_low(const Vec4<R>* posm, uint32_t i) {
+    const Vec4<R> v = ld4(posm + i);
+    if (!finite4(v.x, v.y, v.z, v.w)) return 0xffffffffu;
+    return (uint32_t)(uint64_t)__double_as_longlong(r2_fp64((double)v.x, (double)v.y, (double)v.z));
+}
+
+template <typename R>
+__global__ void tie_fixup_kernel(const uint32_t* __restrict__ key, const Vec4<R>* __restrict__ posm,
                                  uint32_t* __restrict__ val, int64_t N, unsigned* err) {
+    constexpr int kLocal = 16;   // runs up to this length are sorted in registers/L1
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t k = key[i];
@@ -199,18 +325,35 @@ __global__ void tie_fixup_kernel(const uint32_t* __restrict__ key, const uint32_
         int64_t j = i + 1;
         while (j + 1 < N && key[j + 1] == k && j - i < kMaxTieRun) ++j;
         if (j + 1 < N && key[j + 1] == k) { report(err, ETICS_ERR_UNSUPPORTED); continue; }
-        for (int64_t a = i + 1; a <= j; ++a) {
-            const uint32_t va = val[a];
-            const uint32_t la = lo[va];
-            int64_t b = a - 1;
-            while (b >= i) {
-                const uint32_t vb = val[b];
-                const uint32_t lb = lo[vb];
-                if (lb < la || (lb == la && vb < va)) break;
-                val[b + 1] = vb;
-                --b;
+        const int len = (int)(j - i + 1);
+        if (len <= kLocal) {
+            uint32_t lows[kLocal], ids[kLocal];
+            for (int a = 0; a < len; ++a) { ids[a] = val[i + a]; lows[a] = r2_low<R>(posm, ids[a]); }
+            for (int a = 1; a < len; ++a) {
+                const uint32_t va = ids[a], la = lows[a];
+                int b = a - 1;
+                while (b >= 0 && (lows[b] > la || (lows[b] == la && ids[b] > va))) {
+                    ids[b + 1] = ids[b];
+                    lows[b + 1] = lows[b];
+                    --b;
+                }
+                ids[b + 1] = va;
+                lows[b + 1] = la;
             }
-            val[b + 1] = va;
+            for (int a = 0; a < len; ++a) val[i + a] = ids[a];
+        } else {
+            // longer runs (rare): insertion sort in place, low words recomputed
+            for (int64_t a = i + 1; a <= j; ++a) {
+                const uint32_t va = val[a], la = r2_low<R>(posm, va);
+                int64_t b = a - 1;
+                while (b >= i) {
+                    const uint32_t vb = val[b], lb = r2_low<R>(posm, vb);
+                    if (lb < la || (lb == la && vb < va)) break;
+                    val[b + 1] = vb;
+                    --b;
+                }
+                val[b + 1] = va;
+            }
         }
     }
 }
@@ -232,7 +375,6 @@ SortBuffers sort_buffers(void* ws, int64_t N, size_t* total) {
     b.keys_b = reinterpret_cast<uint32_t*>(take(n4));
     b.vals_a = reinterpret_cast<uint32_t*>(take(n4));
     b.vals_b = reinterpret_cast<uint32_t*>(take(n4));
-    b.lo = reinterpret_cast<uint32_t*>(take(n4));
     const size_t nst = (size_t)sort_tiles(N);
     b.zero_bytes = (4 * 256 + 4 * nst * 256 + 64) * 4;
     b.zero_bytes = (b.zero_bytes + 255) / 256 * 256;
@@ -251,7 +393,7 @@ int radial_sort_impl(const void* posm, int64_t N, const SortBuffers& b, const La
     int kg = (int)((N + 255) / 256);
     if (kg > ctx.num_sms * 8) kg = ctx.num_sms * 8;
     keygen_kernel<R><<<kg, 256, 0, ctx.stream>>>(reinterpret_cast<const Vec4<R>*>(posm), N,
-                                                  b.keys_a, b.lo, b.vals_a, b.hist, ctx.err);
+                                                  b.keys_a, b.vals_a, b.hist, ctx.err);
     if (cudaGetLastError()) return ETICS_ERR_CUDA;
     ++*ctx.launches;
     stage_event(ctx, 1);
@@ -269,7 +411,8 @@ int radial_sort_impl(const void* posm, int64_t N, const SortBuffers& b, const La
     // after 4 passes the sorted keys/values are back in keys_a / vals_a
     int fg = (int)((N + 255) / 256);
     if (fg > ctx.num_sms * 8) fg = ctx.num_sms * 8;
-    tie_fixup_kernel<<<fg, 256, 0, ctx.stream>>>(b.keys_a, b.lo, b.vals_a, N, ctx.err);
+    tie_fixup_kernel<R><<<fg, 256, 0, ctx.stream>>>(b.keys_a, reinterpret_cast<const Vec4<R>*>(posm),
+                                                     b.vals_a, N, ctx.err);
     if (cudaGetLastError()) return ETICS_ERR_CUDA;
     ++*ctx.launches;
     return ETICS_OK;

@@ -62,6 +62,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.etics_scf_field.argtypes = [vp, i64, i32, i32, i32, vp, vp, i32, vp]
         lib.etics_mex_field.argtypes = [vp, i64, i32, i32, vp, i32, vp, sz, vp]
         lib.etics_radial_sort.argtypes = [vp, i64, i32, vp, vp, sz, vp]
+        lib.etics_radial_keys.argtypes = [vp, i64, i32, vp, vp]
         lib.etics_leapfrog_step.argtypes = [vp, vp, vp, i64, dbl, i32, i32, i32, i32, vp, vp, sz,
                                             vp]
         lib.etics_get_error.argtypes = [vp]
@@ -70,7 +71,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.etics_launch_count.restype = ctypes.c_uint64
         lib.etics_set_stage_events.argtypes = [ctypes.POINTER(ctypes.c_void_p), i32]
         for name in ("etics_scf_coeffs", "etics_scf_field", "etics_mex_field",
-                     "etics_radial_sort", "etics_leapfrog_step", "etics_get_error",
+                     "etics_radial_sort", "etics_radial_keys", "etics_leapfrog_step",
+                     "etics_get_error",
                      "etics_set_stage_events"):
             getattr(lib, name).restype = i32
         _lib = lib
@@ -201,6 +203,16 @@ def radial_order(posm: torch.Tensor, ws: torch.Tensor | None = None, stream=None
     return order[:n].to(torch.int64) & 0xFFFFFFFF
 
 
+def radial_keys(posm: torch.Tensor, stream=None) -> torch.Tensor:
+    """High 32 bits of the FP64 r^2 bit pattern per particle (int64 tensor)."""
+    posm = _particles(posm, "posm")
+    n = posm.shape[0]
+    keys = torch.empty(max(n, 1), dtype=torch.int32, device=posm.device)
+    _check(load().etics_radial_keys(posm.data_ptr(), n, _precision(posm), keys.data_ptr(),
+                                    _stream(stream)), "etics_radial_keys")
+    return keys[:n].to(torch.int64) & 0xFFFFFFFF
+
+
 def leapfrog_step(posm: torch.Tensor, vel: torch.Tensor, accpot: torch.Tensor, dt: float,
                   method: int, n_max: int, l_max: int, coeffs_out: torch.Tensor | None = None,
                   ws: torch.Tensor | None = None, stream=None) -> None:
@@ -238,13 +250,15 @@ def launch_count() -> int:
 
 
 def set_stage_events(events) -> None:
-    """Record torch.cuda.Event objects at stage boundaries (None disables)."""
+    """Have later calls record these raw cudaEvent_t handles (ints or
+    c_void_p) at their stage boundaries; None disables."""
     lib = load()
     if not events:
         _check(lib.etics_set_stage_events(None, 0), "etics_set_stage_events")
         set_stage_events._keep = None
         return
-    arr = (ctypes.c_void_p * len(events))(*[ctypes.c_void_p(e.cuda_event) for e in events])
+    arr = (ctypes.c_void_p * len(events))(
+        *[e if isinstance(e, ctypes.c_void_p) else ctypes.c_void_p(int(e)) for e in events])
     set_stage_events._keep = arr
     _check(lib.etics_set_stage_events(arr, len(events)), "etics_set_stage_events")
 

@@ -38,6 +38,51 @@ def test_radial_order_is_exact(precision, n):
     assert np.array_equal(o_or, ref)
 
 
+def near_boundary_particles(n, seed):
+    """FP32 particles whose r^2 lies within a few FP64 ulps of a boundary of
+    the 20-bit mantissa buckets of the sort key (and exact squares, zeros,
+    tiny and huge radii)."""
+    rng = np.random.default_rng(seed)
+    e = rng.integers(-40, 40, n)
+    m = rng.integers(1 << 20, 1 << 21, n).astype(np.float64)
+    b = m * 2.0 ** (e - 20)                       # a bucket boundary
+    x = np.sqrt(b).astype(np.float32)
+    pm = np.zeros((n, 4), dtype=np.float32)
+    pm[:, 0] = x
+    k = n // 2
+    pm[:k, 1] = (np.sqrt(b[:k]) * rng.uniform(1e-5, 1e-3, k)).astype(np.float32)
+    pm[:k, 2] = (np.sqrt(b[:k]) * rng.uniform(1e-5, 1e-3, k)).astype(np.float32)
+    pm[:10, :3] = 0.0
+    pm[10:20, 0] = np.float32(1e-30)
+    pm[20:25, 0] = np.float32(3e18)
+    pm[25:30, 0] = np.float32(1e20)           # r^2 overflows FP32
+    pm[30:40, :3] = [3.0, 4.0, 12.0]
+    pm[:, 3] = 1.0
+    return pm.astype(np.float64)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_radial_keys_are_fp64_bits(precision):
+    """The sort key equals the high word of the CPU's FP64 (x*x+y*y)+z*z."""
+    for pm in (near_boundary_particles(200000, 1), hernquist(100000, seed=3)):
+        ref_in = rounded(pm, precision)
+        x = ref_in[:, :3]
+        r2 = (x[:, 0] * x[:, 0] + x[:, 1] * x[:, 1]) + x[:, 2] * x[:, 2]
+        ref = (r2.view(np.uint64) >> np.uint64(32)).astype(np.int64)
+        got = etics.radial_keys(device_particles(pm, precision)).cpu().numpy()
+        etics.check_error()
+        bad = np.nonzero(got != ref)[0]
+        assert bad.size == 0, (bad[:5], got[bad[:5]], ref[bad[:5]])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_radial_order_near_boundaries(precision):
+    pm = near_boundary_particles(50000, 2)
+    got = etics.radial_order(device_particles(pm, precision)).cpu().numpy()
+    etics.check_error()
+    assert np.array_equal(got, oracle_order(rounded(pm, precision)))
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_radial_order_full_size(precision):
     n = 1 << 20
@@ -84,6 +129,25 @@ def test_edge_cases(precision):
             assert np.max(np.abs(o[:, :3] - acc_ref)) <= tol * amax, (len(pm), l_max)
             pmax = max(np.max(np.abs(pot_ref)), 1e-300)
             assert np.max(np.abs(o[:, 3] - pot_ref)) <= tol * pmax, (len(pm), l_max)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_sparse_radii_within_a_thread(precision):
+    """Consecutive particles whose radii grow by 2x each (r^6 moments spanning
+    many decades inside one thread's run and one tile): the inner sums must be
+    accumulated forward, never recovered by subtraction."""
+    rng = np.random.default_rng(21)
+    n = 3000
+    r = np.concatenate([2.0 ** np.arange(-20, 20, 1.0), rng.uniform(0.5, 2.0, n - 40)])
+    v = rng.normal(size=(n, 3))
+    pm = np.zeros((n, 4))
+    pm[:, :3] = v / np.linalg.norm(v, axis=1)[:, None] * r[:, None]
+    pm[:, 3] = rng.uniform(0.5, 1.5, n) / n
+    ref_in = rounded(pm, precision)
+    acc_ref, pot_ref, _ = oracle.mex_field(ref_in[:, :3], ref_in[:, 3], 6)
+    o = etics.mex_field(device_particles(pm, precision), 6).cpu().numpy()
+    etics.check_error()
+    assert_field_close(o, acc_ref, pot_ref, precision, "sparse")
 
 
 def test_output_masks_and_empty():
