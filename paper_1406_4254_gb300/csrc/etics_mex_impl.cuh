@@ -322,7 +322,7 @@ mex_carry_kernel(const double* __restrict__ tile_agg, int ntiles, double* __rest
 // pass 2: in-tile scans + field + scatter
 // ---------------------------------------------------------------------------
 template <typename R, bool ACC>
-__global__ void __launch_bounds__(kMexThreads)
+__global__ void __launch_bounds__(kMexThreads, 4)
 mex_pass2_kernel(const Vec4<R>* __restrict__ sorted, const uint32_t* __restrict__ perm, int64_t N,
                  int l_max, const double* __restrict__ carry, Vec4<R>* __restrict__ out,
                  int out_mask, unsigned* err) {

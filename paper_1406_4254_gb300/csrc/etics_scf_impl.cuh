@@ -72,21 +72,23 @@ __host__ inline size_t scf_coeff_smem(int NR, int l_max, int T, int W, int G) {
 
 // phase 1, angular half: write the unnormalised harmonics of level 0..l_max
 // for particle k into Ys[col][k] (compile-time recursion over the level).
-template <typename R, int L, int LMU>
+// PAD: levels padded to multiples of 4 columns (col_offset_c); otherwise the
+// dense layout, level l starting at column l*l.
+template <typename R, int L, int LMU, bool PAD = true>
 __device__ __forceinline__ void angular_levels(R (&C)[3][LMU + 1], R (&S)[3][LMU + 1], R ux, R uy,
                                                R uz, R uu, int l_max, R* Ys, int T, int k) {
     if constexpr (L <= LMU) {
         if (L > l_max) return;
         constexpr int s0 = L % 3, s1 = (L + 2) % 3, s2 = (L + 1) % 3;
         harm_level<R, L>(C[s1], S[s1], C[s2], S[s2], ux, uy, uz, uu, C[s0], S[s0]);
-        constexpr int co = col_offset_c(L);
+        constexpr int co = PAD ? col_offset_c(L) : L * L;
         Ys[(size_t)(co + 0) * T + k] = C[s0][0];
 #pragma unroll
         for (int m = 1; m <= L; ++m) {
             Ys[(size_t)(co + 2 * m - 1) * T + k] = C[s0][m];
             Ys[(size_t)(co + 2 * m) * T + k] = S[s0][m];
         }
-        angular_levels<R, L + 1, LMU>(C, S, ux, uy, uz, uu, l_max, Ys, T, k);
+        angular_levels<R, L + 1, LMU, PAD>(C, S, ux, uy, uz, uu, l_max, Ys, T, k);
     }
 }
 

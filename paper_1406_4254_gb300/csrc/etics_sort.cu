@@ -83,36 +83,48 @@ __device__ __forceinline__ uint32_t r2_key(double x, double y, double z) {
     return key_from_fp64(r2_fp64(x, y, z));
 }
 
+constexpr int kKeygenIlp = 4;
+
 template <typename R>
 __global__ void __launch_bounds__(256)
 keygen_kernel(const Vec4<R>* __restrict__ posm, int64_t N, uint32_t* __restrict__ key,
-              uint32_t* __restrict__ val, uint32_t* __restrict__ hist, unsigned* err) {
+              uint32_t* __restrict__ hist, unsigned* err) {
     // one private copy of the 4 digit histograms per warp (less atomic contention)
     __shared__ uint32_t sh[8][4 * 256];
     const int warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < 8 * 4 * 256; i += blockDim.x) (&sh[0][0])[i] = 0;
     __syncthreads();
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const Vec4<R> v = ld4(posm + i);
-        uint32_t hi;
-        if (finite4(v.x, v.y, v.z, v.w)) {
-            hi = r2_key(v.x, v.y, v.z);
-        } else {
-            report(err, ETICS_ERR_NONFINITE);
-            hi = 0xffffffffu;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < N;
+         i0 += stride * kKeygenIlp) {
+        Vec4<R> v[kKeygenIlp];
+#pragma unroll
+        for (int u = 0; u < kKeygenIlp; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i < N) v[u] = ld4(posm + i);
         }
-        key[i] = hi;
-        val[i] = (uint32_t)i;
-        atomicAdd(&sh[warp][hi & 255], 1u);
-        atomicAdd(&sh[warp][256 + ((hi >> 8) & 255)], 1u);
-        atomicAdd(&sh[warp][512 + ((hi >> 16) & 255)], 1u);
-        // the top byte (sign + high exponent bits) takes very few values:
-        // aggregate equal digits within the warp before the atomic
-        const uint32_t d3 = hi >> 24;
-        const unsigned same = __match_any_sync(__activemask(), d3);
-        if ((same & ((1u << (threadIdx.x & 31)) - 1u)) == 0u)
-            atomicAdd(&sh[warp][768 + d3], (uint32_t)__popc(same));
+#pragma unroll
+        for (int u = 0; u < kKeygenIlp; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i >= N) break;
+            uint32_t hi;
+            if (finite4(v[u].x, v[u].y, v[u].z, v[u].w)) {
+                hi = r2_key(v[u].x, v[u].y, v[u].z);
+            } else {
+                report(err, ETICS_ERR_NONFINITE);
+                hi = 0xffffffffu;
+            }
+            key[i] = hi;
+            atomicAdd(&sh[warp][hi & 255], 1u);
+            atomicAdd(&sh[warp][256 + ((hi >> 8) & 255)], 1u);
+            atomicAdd(&sh[warp][512 + ((hi >> 16) & 255)], 1u);
+            // the top byte (sign + high exponent bits) takes very few values:
+            // aggregate equal digits within the warp before the atomic
+            const uint32_t d3 = hi >> 24;
+            const unsigned same = __match_any_sync(__activemask(), d3);
+            if ((same & ((1u << (threadIdx.x & 31)) - 1u)) == 0u)
+                atomicAdd(&sh[warp][768 + d3], (uint32_t)__popc(same));
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) {
@@ -200,7 +212,7 @@ onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
         const int64_t idx = start + (int64_t)warp * kSortKpt * 32 + s * 32 + lane;
         if (idx < N) {
             k[s] = keys_in[idx];
-            v[s] = vals_in[idx];
+            v[s] = vals_in ? vals_in[idx] : (uint32_t)idx;   // first pass: identity
             d[s] = (k[s] >> shift) & 255u;
         } else {
             k[s] = 0xffffffffu;
@@ -313,48 +325,89 @@ __device__ __forceinline__ uint32_t r2_low(const Vec4<R>* posm, uint32_t i) {
     return (uint32_t)(uint64_t)__double_as_longlong(r2_fp64((double)v.x, (double)v.y, (double)v.z));
 }
 
+constexpr int kFixThreads = 256;
+constexpr int kFixTile = 2048;
+constexpr int kFixLocal = 16;   // runs up to this length are sorted in registers/L1
+
 template <typename R>
-__global__ void tie_fixup_kernel(const uint32_t* __restrict__ key, const Vec4<R>* __restrict__ posm,
-                                 uint32_t* __restrict__ val, int64_t N, unsigned* err) {
-    constexpr int kLocal = 16;   // runs up to this length are sorted in registers/L1
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t k = key[i];
-        if (i > 0 && key[i - 1] == k) continue;
-        if (i + 1 >= N || key[i + 1] != k) continue;
-        int64_t j = i + 1;
-        while (j + 1 < N && key[j + 1] == k && j - i < kMaxTieRun) ++j;
-        if (j + 1 < N && key[j + 1] == k) { report(err, ETICS_ERR_UNSUPPORTED); continue; }
-        const int len = (int)(j - i + 1);
-        if (len <= kLocal) {
-            uint32_t lows[kLocal], ids[kLocal];
-            for (int a = 0; a < len; ++a) { ids[a] = val[i + a]; lows[a] = r2_low<R>(posm, ids[a]); }
-            for (int a = 1; a < len; ++a) {
-                const uint32_t va = ids[a], la = lows[a];
-                int b = a - 1;
-                while (b >= 0 && (lows[b] > la || (lows[b] == la && ids[b] > va))) {
-                    ids[b + 1] = ids[b];
-                    lows[b + 1] = lows[b];
-                    --b;
-                }
-                ids[b + 1] = va;
-                lows[b + 1] = la;
+__device__ __forceinline__ void sort_run(const Vec4<R>* posm, uint32_t* val, int64_t s, int64_t e) {
+    const int len = (int)(e - s + 1);
+    if (len <= kFixLocal) {
+        uint32_t lows[kFixLocal], ids[kFixLocal];
+        for (int a = 0; a < len; ++a) ids[a] = val[s + a];
+        for (int a = 0; a < len; ++a) lows[a] = r2_low<R>(posm, ids[a]);
+        for (int a = 1; a < len; ++a) {
+            const uint32_t va = ids[a], la = lows[a];
+            int b = a - 1;
+            while (b >= 0 && (lows[b] > la || (lows[b] == la && ids[b] > va))) {
+                ids[b + 1] = ids[b];
+                lows[b + 1] = lows[b];
+                --b;
             }
-            for (int a = 0; a < len; ++a) val[i + a] = ids[a];
-        } else {
-            // longer runs (rare): insertion sort in place, low words recomputed
-            for (int64_t a = i + 1; a <= j; ++a) {
-                const uint32_t va = val[a], la = r2_low<R>(posm, va);
-                int64_t b = a - 1;
-                while (b >= i) {
-                    const uint32_t vb = val[b], lb = r2_low<R>(posm, vb);
-                    if (lb < la || (lb == la && vb < va)) break;
-                    val[b + 1] = vb;
-                    --b;
-                }
-                val[b + 1] = va;
-            }
+            ids[b + 1] = va;
+            lows[b + 1] = la;
         }
+        for (int a = 0; a < len; ++a) val[s + a] = ids[a];
+    } else {
+        // longer runs (rare): insertion sort in place, low words recomputed
+        for (int64_t a = s + 1; a <= e; ++a) {
+            const uint32_t va = val[a], la = r2_low<R>(posm, va);
+            int64_t b = a - 1;
+            while (b >= s) {
+                const uint32_t vb = val[b], lb = r2_low<R>(posm, vb);
+                if (lb < la || (lb == la && vb < va)) break;
+                val[b + 1] = vb;
+                --b;
+            }
+            val[b + 1] = va;
+        }
+    }
+}
+
+// One block per tile of kFixTile sorted positions; the keys of the tile and
+// one position on either side are staged in shared memory.  A run belongs to
+// the tile where it starts.  The block first lists the runs that start in its
+// tile, then sorts them one per thread (so the dependent loads of all runs are
+// in flight together); a run is walked in shared memory and, past the tile
+// end, in global memory.
+template <typename R>
+__global__ void __launch_bounds__(kFixThreads)
+tie_fixup_kernel(const uint32_t* __restrict__ key, const Vec4<R>* __restrict__ posm,
+                 uint32_t* __restrict__ val, int64_t N, unsigned* err) {
+    __shared__ uint32_t s_key[kFixTile + 2];
+    __shared__ int s_runs[kFixTile / 2];
+    __shared__ int s_nruns;
+    const int64_t base = (int64_t)blockIdx.x * kFixTile;
+    const int64_t rem = N - base;
+    const int nt = (int)(rem < kFixTile ? rem : kFixTile);
+    if (threadIdx.x == 0) s_nruns = 0;
+    // s_key[i + 1] = key[base + i] for i in [-1, nt]; sentinels outside [0, N)
+    for (int i = threadIdx.x - 1; i <= nt; i += kFixThreads) {
+        const int64_t g = base + i;
+        uint32_t v;
+        if (g < 0) v = key[0] ^ 1u;             // differs from key[0]
+        else if (g >= N) v = key[N - 1] ^ 1u;   // differs from key[N-1]
+        else v = key[g];
+        s_key[i + 1] = v;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nt; i += kFixThreads) {
+        const uint32_t k = s_key[i + 1];
+        if (s_key[i] != k && s_key[i + 2] == k) s_runs[atomicAdd(&s_nruns, 1)] = i;
+    }
+    __syncthreads();
+    const int nruns = s_nruns;   // at most kFixTile / 2 (each run has >= 2 members)
+    for (int r = threadIdx.x; r < nruns; r += kFixThreads) {
+        const int i = s_runs[r];
+        const uint32_t k = s_key[i + 1];
+        int li = i + 1;
+        while (li + 1 < nt && s_key[li + 2] == k) ++li;
+        int64_t j = base + li;                               // last member so far
+        if (li + 1 >= nt) {                                  // may continue past the tile
+            while (j + 1 < N && key[j + 1] == k && j - (base + i) < kMaxTieRun) ++j;
+        }
+        if (j - (base + i) >= kMaxTieRun) { report(err, ETICS_ERR_UNSUPPORTED); continue; }
+        sort_run<R>(posm, val, base + i, j);
     }
 }
 
@@ -390,10 +443,11 @@ SortBuffers sort_buffers(void* ws, int64_t N, size_t* total) {
 template <typename R>
 int radial_sort_impl(const void* posm, int64_t N, const SortBuffers& b, const LaunchCtx& ctx) {
     if (cudaMemsetAsync(b.zero_base, 0, b.zero_bytes, ctx.stream)) return ETICS_ERR_CUDA;
-    int kg = (int)((N + 255) / 256);
-    if (kg > ctx.num_sms * 8) kg = ctx.num_sms * 8;
+    // few, long-lived blocks: each zeroes and merges 8 private histograms
+    int kg = (int)((N + 256 * kKeygenIlp - 1) / (256 * kKeygenIlp));
+    if (kg > ctx.num_sms * 2) kg = ctx.num_sms * 2;
     keygen_kernel<R><<<kg, 256, 0, ctx.stream>>>(reinterpret_cast<const Vec4<R>*>(posm), N,
-                                                  b.keys_a, b.vals_a, b.hist, ctx.err);
+                                                  b.keys_a, b.hist, ctx.err);
     if (cudaGetLastError()) return ETICS_ERR_CUDA;
     ++*ctx.launches;
     stage_event(ctx, 1);
@@ -401,18 +455,17 @@ int radial_sort_impl(const void* posm, int64_t N, const SortBuffers& b, const La
     uint32_t *kin = b.keys_a, *vin = b.vals_a, *kout = b.keys_b, *vout = b.vals_b;
     for (int pass = 0; pass < 4; ++pass) {
         onesweep_kernel<<<nst, kSortThreads, 0, ctx.stream>>>(
-            kin, vin, kout, vout, b.hist + pass * 256, b.status + (size_t)pass * nst * 256,
-            b.counters + pass, 8 * pass, N, ctx.err);
+            kin, pass == 0 ? nullptr : vin, kout, vout, b.hist + pass * 256,
+            b.status + (size_t)pass * nst * 256, b.counters + pass, 8 * pass, N, ctx.err);
         if (cudaGetLastError()) return ETICS_ERR_CUDA;
         ++*ctx.launches;
         uint32_t* t = kin; kin = kout; kout = t;
         t = vin; vin = vout; vout = t;
     }
     // after 4 passes the sorted keys/values are back in keys_a / vals_a
-    int fg = (int)((N + 255) / 256);
-    if (fg > ctx.num_sms * 8) fg = ctx.num_sms * 8;
-    tie_fixup_kernel<R><<<fg, 256, 0, ctx.stream>>>(b.keys_a, reinterpret_cast<const Vec4<R>*>(posm),
-                                                     b.vals_a, N, ctx.err);
+    const int fg = (int)((N + kFixTile - 1) / kFixTile);
+    tie_fixup_kernel<R><<<fg, kFixThreads, 0, ctx.stream>>>(
+        b.keys_a, reinterpret_cast<const Vec4<R>*>(posm), b.vals_a, N, ctx.err);
     if (cudaGetLastError()) return ETICS_ERR_CUDA;
     ++*ctx.launches;
     return ETICS_OK;
