@@ -122,6 +122,26 @@ int etics_leapfrog_step(void *posm, void *vel, void *accpot, int64_t N, double d
                         int method, int n_max, int l_max, int precision, double *coeffs_out,
                         void *ws, size_t ws_bytes, void *stream);
 
+/* Size of the fixed scratch array behind etics_scf_coeffs_noalloc. */
+#define ETICS_STATIC_SCRATCH_BYTES (4u << 20)
+
+/* The SCF coefficient pass without a caller workspace (the paper has no
+ * counterpart; it exists for callers that cannot allocate device memory or
+ * pass a device buffer, e.g. a hard real-time loop where an allocation could
+ * block or fail, or a host application that owns all device memory and gives
+ * plug-in code no allocation rights).  Same arguments and result as
+ * etics_scf_coeffs minus ws/ws_bytes; allocates nothing.  Its scratch is a
+ * fixed array of ETICS_STATIC_SCRATCH_BYTES that every GPU loading the library
+ * holds until process exit; it returns ETICS_ERR_WORKSPACE when
+ * etics_workspace_bytes(N, n_max, l_max, ETICS_SCF, precision) exceeds it
+ * (e.g. n_max = 16, l_max = 14 on a 152-SM GB300).  The first call on a device
+ * looks up the array's device address with that device current; make that
+ * first call before any stream capture.  All calls share the one array:
+ * calls that overlap on the GPU (different streams, or different host
+ * threads) race and give wrong coefficients. */
+int etics_scf_coeffs_noalloc(const void *posm, int64_t N, int n_max, int l_max, int precision,
+                             double *coeffs, void *stream);
+
 /* Waits for `stream`, then returns and clears the device error word
  * (ETICS_OK if no kernel reported a data error since the last call). */
 int etics_get_error(void *stream);

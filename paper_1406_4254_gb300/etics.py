@@ -63,6 +63,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.etics_mex_field.argtypes = [vp, i64, i32, i32, vp, i32, vp, sz, vp]
         lib.etics_radial_sort.argtypes = [vp, i64, i32, vp, vp, sz, vp]
         lib.etics_radial_keys.argtypes = [vp, i64, i32, vp, vp]
+        lib.etics_scf_coeffs_noalloc.argtypes = [vp, i64, i32, i32, i32, vp, vp]
         lib.etics_leapfrog_step.argtypes = [vp, vp, vp, i64, dbl, i32, i32, i32, i32, vp, vp, sz,
                                             vp]
         lib.etics_get_error.argtypes = [vp]
@@ -72,6 +73,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.etics_set_stage_events.argtypes = [ctypes.POINTER(ctypes.c_void_p), i32]
         for name in ("etics_scf_coeffs", "etics_scf_field", "etics_mex_field",
                      "etics_radial_sort", "etics_radial_keys", "etics_leapfrog_step",
+                     "etics_scf_coeffs_noalloc",
                      "etics_get_error",
                      "etics_set_stage_events"):
             getattr(lib, name).restype = i32
@@ -145,6 +147,20 @@ def scf_coeffs(posm: torch.Tensor, n_max: int, l_max: int, out: torch.Tensor | N
     wp, wb = _aligned_ptr(ws)
     _check(load().etics_scf_coeffs(posm.data_ptr(), n, n_max, l_max, prec, out.data_ptr(), wp, wb,
                                    _stream(stream)), "etics_scf_coeffs")
+    return out
+
+
+def scf_coeffs_noalloc(posm: torch.Tensor, n_max: int, l_max: int,
+                       out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """SCF coefficients through etics_scf_coeffs_noalloc: no workspace is
+    passed and the library allocates nothing (its scratch is a fixed array
+    inside the library; concurrent calls on the same GPU race)."""
+    posm = _particles(posm, "posm")
+    if out is None:
+        out = torch.empty((n_max + 1, (l_max + 1) ** 2), dtype=torch.float64, device=posm.device)
+    _check(load().etics_scf_coeffs_noalloc(posm.data_ptr(), posm.shape[0], n_max, l_max,
+                                           _precision(posm), out.data_ptr(), _stream(stream)),
+           "etics_scf_coeffs_noalloc")
     return out
 
 
