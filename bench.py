@@ -503,6 +503,20 @@ def run_batch(args):
         t1.record()
         torch.cuda.synchronize()
         tl.append(t0.elapsed_time(t1))
+    # the same per-system calls captured into one graph (launch overhead removed)
+    g2 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g2):
+        loop()
+    for _ in range(2):
+        g2.replay()
+    torch.cuda.synchronize()
+    tg = []
+    for _ in range(max(3, args.steps // 2)):
+        t0.record()
+        g2.replay()
+        t1.record()
+        torch.cuda.synchronize()
+        tg.append(t0.elapsed_time(t1))
     etics.check_error()
     # agreement of the two paths
     err = 0.0
@@ -517,7 +531,10 @@ def run_batch(args):
                               "kernel_launches": 3},
             "one_call_per_system": {"ms": ml, "particle_forces_per_s": ntot / (ml * 1e-3),
                                     "kernel_launches": 3 * len(sizes)},
-            "speedup": ml / mb, "tuning": tuning.as_dict(), "tuned_in_this_run": tuned_now,
+            "one_call_per_system_graph": {"ms": statistics.mean(tg),
+                                          "particle_forces_per_s": ntot / (statistics.mean(tg) * 1e-3)},
+            "speedup": ml / mb, "speedup_vs_graph_of_calls": statistics.mean(tg) / mb,
+            "tuning": tuning.as_dict(), "tuned_in_this_run": tuned_now,
             "max_rel_coeff_diff_batched_vs_single": err}
 
 

@@ -113,6 +113,38 @@ int etics_radial_sort(const void *posm, int64_t N, int precision, uint32_t *orde
  * keys: device uint32[N].  Needs no workspace. */
 int etics_radial_keys(const void *posm, int64_t N, int precision, uint32_t *keys, void *stream);
 
+/* ---- batches of independent systems ------------------------------------
+ * Many independent systems of uneven size and expansion order in one SCF pass
+ * (the paper notes the GPU is under-loaded at small N, Sec. 3.4): the
+ * particles of all systems are concatenated in posm, system i owning
+ * items[i].n consecutive particles; its coefficients are packed one system
+ * after another (n_max+1)(l_max+1)^2 each, in the layout of etics_scf_coeffs. */
+typedef struct { int64_t n; int n_max; int l_max; } etics_batch_item;
+/* Launch shape (0 = default): particles per coefficient tile (multiple of 4,
+ * 8..128; FP64 plans with tile > 64 exceed one block's shared memory and are
+ * rejected with ETICS_ERR_UNSUPPORTED), coefficient blocks per SM (1..8),
+ * field threads per block (multiple of 32, <= 256), particles per field work
+ * item (>= 1). */
+typedef struct { int tile; int blocks_per_sm; int field_threads; int field_chunk; } etics_batch_tuning;
+
+/* Builds the batch plan in HOST memory.  With plan == NULL only the sizes are
+ * returned: *plan_bytes_needed (plan size), *ws_bytes (device workspace) and
+ * *coeff_count (doubles of packed coefficients).  Limits per system:
+ * n_max <= 14, l_max <= 8.  The caller copies the plan to device memory and
+ * passes both copies to etics_scf_batch. */
+int etics_scf_batch_plan(const etics_batch_item *items, int ninst,
+                         const etics_batch_tuning *tuning, int precision, void *plan,
+                         size_t plan_bytes, size_t *plan_bytes_needed, size_t *ws_bytes,
+                         int64_t *coeff_count);
+
+/* SCF coefficients and field of every system of the plan: three kernels
+ * (coefficients, ordered finalize, field), no host synchronisation, so the
+ * call can be captured into a CUDA graph.  accpot may be NULL (coefficients
+ * only).  ws: at least the plan's ws_bytes. */
+int etics_scf_batch(const void *posm, const void *plan_host, const void *plan_dev, int precision,
+                    double *coeffs, void *accpot, int out_mask, void *ws, size_t ws_bytes,
+                    void *stream);
+
 /* One kick-drift-kick leapfrog step (Sec. 3.4, Sec. 5.4), in place:
  *   v += dt/2 a;  x += dt v;  (a, Phi) = force(x) by `method`;  v += dt/2 a.
  * accpot holds a(x) on entry and (a, Phi) at the new positions on exit.

@@ -210,6 +210,40 @@ int etics_leapfrog_step(void* posm, void* vel, void* accpot, int64_t N, double d
                  : etics::kick_f64(vel, accpot, N, dt, h.ctx);
 }
 
+int etics_scf_batch_plan(const etics_batch_item* items, int ninst,
+                         const etics_batch_tuning* tuning, int precision, void* plan,
+                         size_t plan_bytes, size_t* plan_bytes_needed, size_t* ws_bytes,
+                         int64_t* coeff_count) {
+    if (!valid_precision(precision) || ninst <= 0 || !items || !plan_bytes_needed)
+        return ETICS_ERR_ARG;
+    unsigned* err = nullptr;
+    int sms = 0;
+    const int rc = current_device_state(&err, &sms);
+    if (rc) return rc;
+    return etics::batch_plan_build(items, ninst, tuning, sms, precision, plan, plan_bytes,
+                                   plan_bytes_needed, ws_bytes, coeff_count);
+}
+
+int etics_scf_batch(const void* posm, const void* plan_host, const void* plan_dev, int precision,
+                    double* coeffs, void* accpot, int out_mask, void* ws, size_t ws_bytes,
+                    void* stream) {
+    if (!valid_precision(precision) || !plan_host || !plan_dev || !coeffs || !ws) return ETICS_ERR_ARG;
+    if (!aligned(posm, 16) || !aligned(coeffs, 8) || !aligned(ws, 256) || !aligned(plan_dev, 16))
+        return ETICS_ERR_ARG;
+    if (accpot && (!aligned(accpot, 16) || (out_mask & (ETICS_OUT_ACC | ETICS_OUT_POT)) == 0 ||
+                   (out_mask & ~3)))
+        return ETICS_ERR_ARG;
+    CtxHolder h;
+    int rc = make_ctx(stream, h);
+    if (rc) return rc;
+    etics::stage_event(h.ctx, 0);
+    return precision == ETICS_MIXED
+               ? etics::batch_launch<float>(posm, plan_host, plan_dev, coeffs, accpot, out_mask, ws,
+                                            ws_bytes, h.ctx)
+               : etics::batch_launch<double>(posm, plan_host, plan_dev, coeffs, accpot, out_mask,
+                                             ws, ws_bytes, h.ctx);
+}
+
 int etics_get_error(void* stream) {
     unsigned* err = nullptr;
     int sms = 0;

@@ -45,6 +45,14 @@ int mex_field_f64(const void* posm, int64_t N, int l_max, void* out, int out_mas
 int radial_order_f32(const void* posm, int64_t N, uint32_t* order, void* ws, const LaunchCtx& ctx);
 int radial_order_f64(const void* posm, int64_t N, uint32_t* order, void* ws, const LaunchCtx& ctx);
 
+// ---- batches (etics_batch.cu) ------------------------------------------------
+int batch_plan_build(const etics_batch_item* items, int ninst, const etics_batch_tuning* tuning,
+                     int num_sms, int precision, void* plan, size_t plan_bytes, size_t* need,
+                     size_t* ws_bytes, int64_t* coef_total);
+template <typename R>
+int batch_launch(const void* posm, const void* plan_host, const void* plan_dev, double* coeffs,
+                 void* out, int out_mask, void* ws, size_t ws_bytes, const LaunchCtx& ctx);
+
 // ---- leapfrog (etics_step.cu) ----------------------------------------------
 int kick_drift_f32(void* posm, void* vel, const void* acc, int64_t N, double dt,
                    const LaunchCtx& ctx);

@@ -64,6 +64,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.etics_radial_sort.argtypes = [vp, i64, i32, vp, vp, sz, vp]
         lib.etics_radial_keys.argtypes = [vp, i64, i32, vp, vp]
         lib.etics_scf_coeffs_noalloc.argtypes = [vp, i64, i32, i32, i32, vp, vp]
+        lib.etics_scf_batch_plan.argtypes = [vp, i32, vp, i32, vp, sz, ctypes.POINTER(sz),
+                                             ctypes.POINTER(sz), ctypes.POINTER(i64)]
+        lib.etics_scf_batch.argtypes = [vp, vp, vp, i32, vp, vp, i32, vp, sz, vp]
         lib.etics_leapfrog_step.argtypes = [vp, vp, vp, i64, dbl, i32, i32, i32, i32, vp, vp, sz,
                                             vp]
         lib.etics_get_error.argtypes = [vp]
@@ -73,7 +76,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.etics_set_stage_events.argtypes = [ctypes.POINTER(ctypes.c_void_p), i32]
         for name in ("etics_scf_coeffs", "etics_scf_field", "etics_mex_field",
                      "etics_radial_sort", "etics_radial_keys", "etics_leapfrog_step",
-                     "etics_scf_coeffs_noalloc",
+                     "etics_scf_coeffs_noalloc", "etics_scf_batch_plan", "etics_scf_batch",
                      "etics_get_error",
                      "etics_set_stage_events"):
             getattr(lib, name).restype = i32
@@ -248,6 +251,83 @@ def leapfrog_step(posm: torch.Tensor, vel: torch.Tensor, accpot: torch.Tensor, d
     _check(load().etics_leapfrog_step(posm.data_ptr(), vel.data_ptr(), accpot.data_ptr(), n,
                                       float(dt), method, n_max, l_max, prec, cp, wp, wb,
                                       _stream(stream)), "etics_leapfrog_step")
+
+
+class _BatchItem(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("n_max", ctypes.c_int), ("l_max", ctypes.c_int)]
+
+
+class BatchTuning(ctypes.Structure):
+    """Launch shape of a batch (0 = library default)."""
+    _fields_ = [("tile", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
+                ("field_threads", ctypes.c_int), ("field_chunk", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class BatchPlan:
+    """A batch plan: host bytes, their device copy, workspace, and the packed
+    coefficient offsets of every system."""
+
+    def __init__(self, sizes, n_maxes, l_maxes, precision=MIXED, tuning=None, device=None):
+        lib = load()
+        ninst = len(sizes)
+        items = (_BatchItem * ninst)(*[_BatchItem(int(n), int(a), int(b))
+                                       for n, a, b in zip(sizes, n_maxes, l_maxes)])
+        need, ws, cc = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_int64()
+        tp = ctypes.addressof(tuning) if tuning is not None else None
+        _check(lib.etics_scf_batch_plan(ctypes.addressof(items), ninst, tp, precision, None, 0,
+                                        ctypes.byref(need), ctypes.byref(ws), ctypes.byref(cc)),
+               "etics_scf_batch_plan")
+        self.host = (ctypes.c_uint8 * need.value)()
+        _check(lib.etics_scf_batch_plan(ctypes.addressof(items), ninst, tp, precision,
+                                        ctypes.addressof(self.host), need.value,
+                                        ctypes.byref(need), ctypes.byref(ws), ctypes.byref(cc)),
+               "etics_scf_batch_plan")
+        dev = torch.device(device) if device is not None else torch.device(
+            "cuda", torch.cuda.current_device())
+        self.dev = torch.frombuffer(bytearray(self.host), dtype=torch.uint8).to(dev)
+        self.ws = torch.empty(ws.value + 256, dtype=torch.uint8, device=dev)
+        self.coeff_count = int(cc.value)
+        self.precision = precision
+        self.sizes = [int(n) for n in sizes]
+        self.n_maxes = [int(a) for a in n_maxes]
+        self.l_maxes = [int(b) for b in l_maxes]
+        offs, o = [], 0
+        for a, b in zip(self.n_maxes, self.l_maxes):
+            offs.append(o)
+            o += (a + 1) * (b + 1) ** 2
+        self.coeff_offsets = offs
+        self.particle_offsets = [0]
+        for n in self.sizes:
+            self.particle_offsets.append(self.particle_offsets[-1] + n)
+
+    def coeffs_of(self, packed: torch.Tensor, i: int) -> torch.Tensor:
+        a, b = self.n_maxes[i], self.l_maxes[i]
+        o = self.coeff_offsets[i]
+        return packed[o:o + (a + 1) * (b + 1) ** 2].view(a + 1, (b + 1) ** 2)
+
+
+def scf_batch(posm: torch.Tensor, plan: BatchPlan, coeffs: torch.Tensor | None = None,
+              out: torch.Tensor | None = None, out_mask: int = OUT_ACC | OUT_POT,
+              with_field: bool = True, stream=None):
+    """SCF coefficients (packed float64) and field of every system of the plan."""
+    posm = _particles(posm, "posm")
+    if _precision(posm) != plan.precision:
+        raise TypeError("particle dtype does not match the plan's precision")
+    if posm.shape[0] != plan.particle_offsets[-1]:
+        raise ValueError("posm does not hold the plan's particles")
+    if coeffs is None:
+        coeffs = torch.empty(max(plan.coeff_count, 1), dtype=torch.float64, device=posm.device)
+    if with_field and out is None:
+        out = torch.empty_like(posm)
+    wp, wb = _aligned_ptr(plan.ws)
+    _check(load().etics_scf_batch(posm.data_ptr(), ctypes.addressof(plan.host),
+                                  plan.dev.data_ptr(), plan.precision, coeffs.data_ptr(),
+                                  out.data_ptr() if with_field else None, out_mask, wp, wb,
+                                  _stream(stream)), "etics_scf_batch")
+    return coeffs, out
 
 
 def get_error(stream=None) -> int:

@@ -50,7 +50,7 @@ def hernquist(n: int, seed: int = 0, axes=(1.0, 1.0, 1.0)) -> np.ndarray:
     x = x * np.asarray(axes, dtype=np.float64)[None, :]
     out = np.empty((n, 4))
     out[:, :3] = x
-    out[:, 3] = 1.0 / n
+    out[:, 3] = 1.0 / max(n, 1)
     return out
 
 
