@@ -17,9 +17,13 @@ Dynamical Simulations"):
 * ``direct``: Sec. 2.1 eq. 4.
 * ``leapfrog_step``: the kick-drift-kick step mentioned in Secs. 3.4 and 5.4.
 
+``oracle.mlp`` (numpy) is the FP64 oracle of the coefficient-forecasting MLP
+and its feature / update glue; the paper has no learned part.
+
 Parity: every function here is pinned by ``tests/test_oracle_*.py`` against
-closed forms, quadrature identities, brute force or invariants (none is
-"parity unpinned").
+closed forms, quadrature identities, brute force or invariants, and every
+function of ``oracle.mlp`` by ``tests/test_oracle_mlp.py`` (none is "parity
+unpinned").
 """
 from __future__ import annotations
 
