@@ -538,6 +538,154 @@ def run_batch(args):
             "max_rel_coeff_diff_batched_vs_single": err}
 
 
+def run_surrogate(args):
+    """Surrogate-accelerated SCF: a Hernquist sphere with a 5% l = 2, m = 2
+    bar perturbation (N = 2^26 by default), SCF (14, 8), KDK at dt = 0.005.
+    A plain-SCF run of --sur-steps steps produces the coefficient trajectory;
+    the per-coefficient MLP (8 -> 256 -> 256 -> 1, bf16 weights, FP32
+    accumulation) is trained on its first 75% by the library's kernels and
+    validated one step ahead on the rest.  From the final state three
+    continuations of --sur-eval steps are timed: plain SCF every step, the
+    forecast on 3 of every 4 steps (plain SCF on the 4th, judging the forecast
+    against the force-error budget: median <= 1e-5, 99th percentile <= 1e-4,
+    on 4096 particles), and plain reuse of the last coefficients on 3 of 4
+    steps (judged the same way).  An
+    untimed pass then measures each substep's relative force error (eq. 23)
+    against plain SCF at the same positions on a 65536-particle sample."""
+    import torch
+    from paper_1406_4254_gb300 import etics, inputs, surrogate
+    dev = torch.device("cuda", 0)
+    n, n_max, l_max, dt = args.sur_n, 14, 8, 0.005
+    t0 = time.time()
+    pm, vel = inputs.hernquist_bar(n, seed=args.seed, eps=0.05)
+    t_ic = time.time() - t0
+    x = torch.tensor(pm, dtype=torch.float32, device=dev)
+    v = torch.zeros_like(x)
+    v[:, :3] = torch.tensor(vel, dtype=torch.float32, device=dev)
+    del pm, vel
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    traj, acc = surrogate.coefficient_trajectory(x, v, args.sur_steps, dt, n_max, l_max)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms_traj = ev0.elapsed_time(ev1) / args.sur_steps
+    T = traj.shape[0]
+    n_train = int(0.75 * T)
+    fc = surrogate.Forecaster(n_max, l_max, hidden=256, seed=args.seed)
+    ev0.record()
+    losses = fc.fit(traj[:n_train], iters=args.sur_iters, batch=16, lr=1e-3, seed=args.seed,
+                    log_every=max(1, args.sur_iters // 10))
+    ev1.record()
+    torch.cuda.synchronize()
+    ms_train = ev0.elapsed_time(ev1)
+    hold, lin, cubic, net = fc.one_step_errors(traj, n_train)
+    med = lambda a: float(np.median(a))  # noqa: E731
+    m = x[:, 3].double()
+
+    def energy(vv, aa):
+        return float(0.5 * (m * (vv[:, :3].double() ** 2).sum(1)).sum()
+                     + 0.5 * (m * aa[:, 3].double()).sum())
+
+    modes = {}
+    for mode in ("plain", "forecast", "hold"):
+        xs, vs, accs = x.clone(), v.clone(), acc.clone()
+        fc.reset(traj)
+        e0 = energy(vs, accs)
+        torch.cuda.synchronize()
+        ev0.record()
+        if mode == "plain":
+            for _ in range(args.sur_eval):
+                etics.leapfrog_step(xs, vs, accs, dt, etics.SCF, n_max, l_max)
+            st = None
+        else:
+            st = surrogate.run(xs, vs, accs, args.sur_eval, dt, fc, period=4, mode=mode)
+        ev1.record()
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / args.sur_eval
+        modes[mode] = {"ms_per_step": ms, "particle_steps_per_s": n / (ms * 1e-3),
+                       "energy_drift": abs(energy(vs, accs) / e0 - 1.0)}
+        if st is not None:
+            modes[mode].update({"recomputes": st.recomputes, "forecast_steps": st.forecasts,
+                                "fallback_blocks": st.fallbacks,
+                                "checks": len(st.checks),
+                                "check_frac_above_median_budget": med([c[1] for c in st.checks[1:]])
+                                if len(st.checks) > 1 else None,
+                                "check_frac_above_p99_budget": med([c[2] for c in st.checks[1:]])
+                                if len(st.checks) > 1 else None})
+        del xs, vs, accs
+    for mode in ("forecast", "hold"):
+        modes[mode]["speedup_vs_plain"] = modes["plain"]["ms_per_step"] / modes[mode]["ms_per_step"]
+    # untimed accuracy pass: every substep against plain SCF at the same positions
+    s_n = min(65536, n)
+    for mode in ("forecast", "hold"):
+        xs, vs, accs = x.clone(), v.clone(), acc.clone()
+        fc.reset(traj)
+        per_sub = {1: [], 2: [], 3: []}
+        a_ref = torch.empty((s_n, 4), dtype=torch.float32, device=dev)
+        a_use = torch.empty_like(a_ref)
+
+        def hook(t, kind, c_use):
+            if kind == "recompute":
+                return
+            c_true = etics.scf_coeffs(xs, n_max, l_max)
+            etics.scf_field(xs[:s_n], c_true, n_max, l_max, out=a_ref)
+            etics.scf_field(xs[:s_n], c_use.view(n_max + 1, -1), n_max, l_max, out=a_use)
+            a = a_use.double().cpu().numpy()[:, :3]
+            r = a_ref.double().cpu().numpy()[:, :3]
+            e = np.linalg.norm(a - r, axis=1) / np.linalg.norm(r, axis=1)
+            per_sub[t % 4].append((float(np.median(e)), float(np.quantile(e, 0.99)),
+                                   float(e.max())))
+
+        surrogate.run(xs, vs, accs, min(args.sur_eval, 200), dt, fc, period=4, mode=mode,
+                      hook=hook)
+        modes[mode]["force_error_by_substep"] = {
+            str(k): {"median": med([p[0] for p in v_]), "p99": med([p[1] for p in v_]),
+                     "max": float(max(p[2] for p in v_)), "samples": len(v_)}
+            for k, v_ in per_sub.items() if v_}
+        del xs, vs, accs
+    # split of the plain step: coefficient pass vs field pass at the final state
+    c_fin = etics.scf_coeffs(x, n_max, l_max)
+    for _ in range(2):
+        etics.scf_field(x, c_fin, n_max, l_max, out=acc)
+    ev0.record()
+    for _ in range(5):
+        etics.scf_coeffs(x, n_max, l_max, out=c_fin)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms_coef = ev0.elapsed_time(ev1) / 5
+    ev0.record()
+    for _ in range(5):
+        etics.scf_field(x, c_fin, n_max, l_max, out=acc)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms_field = ev0.elapsed_time(ev1) / 5
+    # the plain FP64 form for reference (a few steps)
+    x64, v64 = x.double(), v.double()
+    acc64, _ = etics.scf_force(x64, n_max, l_max)
+    k64 = 3
+    ev0.record()
+    for _ in range(k64):
+        etics.leapfrog_step(x64, v64, acc64, dt, etics.SCF, n_max, l_max)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms64 = ev0.elapsed_time(ev1) / k64
+    etics.check_error()
+    return {"experiment": "surrogate",
+            "workload": f"hernquist + 5% l=2 m=2 bar, N={n}, SCF(14,8), KDK dt={dt}",
+            "trajectory": {"steps": args.sur_steps, "plain_ms_per_step": ms_traj,
+                           "initial_conditions_s": t_ic},
+            "training": {"network": "per-coefficient 8->256->256->1, tanh, bf16 x bf16 -> FP32",
+                         "train_vectors": n_train, "iters": args.sur_iters,
+                         "histories_per_batch": 16, "ms": ms_train, "loss_log": losses},
+            "one_step_error_validation": {"hold": med(hold), "linear": med(lin),
+                                          "cubic": med(cubic), "mlp": med(net),
+                                          "unit": "|c_hat - c| / |c - c_prev|, median"},
+            "budget": {"median": 1e-5, "p99": 1e-4, "sample": 4096, "period": 4},
+            "rollout_steps": args.sur_eval, "modes": modes,
+            "plain_fp64": {"ms_per_step": ms64, "steps": k64},
+            "plain_mixed_split_ms": {"coefficients": ms_coef, "field": ms_field}}
+
+
 def emit(obj):
     print(json.dumps(obj), flush=True)
 
@@ -553,9 +701,16 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=65536)
-    ap.add_argument("--experiment", choices=["leapfrog", "batch"], default=None)
+    ap.add_argument("--experiment", choices=["leapfrog", "batch", "surrogate"], default=None)
     ap.add_argument("--lf-steps", type=int, default=100)
+    ap.add_argument("--sur-n", type=int, default=1 << 26)
+    ap.add_argument("--sur-steps", type=int, default=2000)
+    ap.add_argument("--sur-eval", type=int, default=400)
+    ap.add_argument("--sur-iters", type=int, default=3000)
     args = ap.parse_args()
+    if args.experiment == "surrogate":
+        emit(run_surrogate(args))
+        return
     if args.experiment == "leapfrog":
         emit(run_leapfrog(args))
         return

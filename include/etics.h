@@ -174,6 +174,98 @@ int etics_leapfrog_step(void *posm, void *vel, void *accpot, int64_t N, double d
 int etics_scf_coeffs_noalloc(const void *posm, int64_t N, int n_max, int l_max, int precision,
                              double *coeffs, void *stream);
 
+/* One kick-drift-kick step like etics_leapfrog_step with method SCF, but the
+ * force at the new positions uses the given coefficients (c[n][l*l+l+m],
+ * device, (n_max+1)(l_max+1)^2 doubles) instead of a coefficient pass: the
+ * step that a coefficient forecast drives.  Needs no workspace. */
+int etics_leapfrog_step_coeffs(void *posm, void *vel, void *accpot, int64_t N, double dt,
+                               int n_max, int l_max, int precision, const double *coeffs,
+                               void *stream);
+
+/* ---- coefficient-forecasting MLP ----------------------------------------
+ * Not in the paper.  It extends the reuse of coefficients over several steps
+ * (temporal softening, end of Sec. 4.1) to a forecast: a multilayer
+ * perceptron maps the last 8 coefficient vectors to the next one, so that the
+ * coefficient pass can be skipped on most steps.
+ *
+ * Network: dims[0] -> dims[1] -> ... -> dims[nlayers]; tanh after every layer
+ * but the last.  params: device FP32, for each layer i W_i (dims[i] x
+ * dims[i+1], row-major, input index first) then b_i (dims[i+1]);
+ * params_bf16: device bf16 codes (uint16) of the same vector, the operands of
+ * the tensor-core products (bf16 x bf16, FP32 accumulation).  x: device bf16
+ * codes, batch x dims[0] row-major; y / target: device FP32, batch x
+ * dims[nlayers].  All results are deterministic (fixed summation orders). */
+#define ETICS_MLP_MAX_LAYERS 4
+typedef struct { int nlayers; int dims[ETICS_MLP_MAX_LAYERS + 1]; } etics_mlp_shape;
+
+/* Floats in params (-1 for an invalid shape: nlayers outside 1..4 or a
+ * width outside 1..2^20). */
+int64_t etics_mlp_param_count(const etics_mlp_shape *shape);
+/* Device workspace of etics_mlp_forward / etics_mlp_loss_grad for `batch` rows
+ * (0 for an invalid shape). */
+size_t etics_mlp_workspace_bytes(const etics_mlp_shape *shape, int batch);
+/* y = network(x). */
+int etics_mlp_forward(const etics_mlp_shape *shape, const float *params,
+                      const uint16_t *params_bf16, const uint16_t *x, int batch, float *y,
+                      void *ws, size_t ws_bytes, void *stream);
+/* *loss (device double) = mean over batch x dims[nlayers] of (y - target)^2
+ * and grads (device FP32, the layout of params) = its gradient by
+ * back-propagation.  batch >= 1. */
+int etics_mlp_loss_grad(const etics_mlp_shape *shape, const float *params,
+                        const uint16_t *params_bf16, const uint16_t *x, const float *target,
+                        int batch, float *grads, double *loss, void *ws, size_t ws_bytes,
+                        void *stream);
+/* One Adam step (t >= 1: the step count, for the bias corrections) on params
+ * with moment buffers m, v (device FP32, zero before the first step); also
+ * refreshes params_bf16. */
+int etics_mlp_adam(const etics_mlp_shape *shape, float *params, const float *grads, float *m,
+                   float *v, int64_t t, float lr, float beta1, float beta2, float eps,
+                   uint16_t *params_bf16, void *stream);
+/* params_bf16 = bf16(params) (round to nearest even). */
+int etics_mlp_to_bf16(const etics_mlp_shape *shape, const float *params, uint16_t *params_bf16,
+                      void *stream);
+
+/* Normalisers of a coefficient trajectory traj (device, T x D doubles, T >= 5)
+ * into norm (device, 7 x D doubles): mean, 1/standard deviation, 1/RMS of the
+ * k-th backward differences for k = 1..4, and the RMS s4 of the fourth
+ * differences (a reciprocal is 0 where its scale is 0). */
+int etics_coeff_stats(const double *traj, int T, int D, double *norm, void *stream);
+/* Network inputs x (bf16 codes) of the histories store[rows[b][0..7]]
+ * (device int32, oldest first; store: device, rows of D doubles), eight
+ * blocks per coefficient from the backward differences d1..d4 of the history:
+ * block 0 the normalised state, blocks 1-3 the newest d1, d2, d3, blocks 4-7
+ * the four newest d4, newest first, each over its RMS.  layout
+ * ETICS_FEAT_JOINT: x is batch x 8D, element [b][blk*D + j] (one network row
+ * sees every coefficient); ETICS_FEAT_PER_COEFF: x is (batch*D) x 8, element
+ * [b*D + j][blk] (one row per coefficient, a network shared by all
+ * coefficients).  With next_rows (nullable, device int32[batch]) also the
+ * training targets (batch x D FP32 in both layouts): the next fourth
+ * difference over its RMS, i.e. what cubic extrapolation misses. */
+#define ETICS_FEAT_JOINT 0
+#define ETICS_FEAT_PER_COEFF 1
+int etics_coeff_features(const double *store, const int32_t *rows, const int32_t *next_rows,
+                         int batch, int D, const double *norm, int layout, uint16_t *x,
+                         float *target, void *stream);
+/* The next coefficient vector of a ring of 8 (ring: device 8 x D doubles;
+ * order: device int32[8], slots oldest..newest): coeffs_in when non-NULL, else
+ * the cubic extrapolation c7 + d1 + d2 + d3 of the ring plus s4 * y, from the
+ * network output y (device FP32[D]; exactly one of coeffs_in, y).  With
+ * commit != 0 the vector is written into the oldest slot and order rotated in
+ * place; coeffs_out (nullable when commit != 0) receives it.  One block;
+ * graph-capturable. */
+int etics_coeff_advance(double *ring, int32_t *order, int D, const double *coeffs_in,
+                        const float *y, const double *norm, double *coeffs_out, int commit,
+                        void *stream);
+
+/* Relative acceleration error e_i = |a_i - r_i| / |r_i| (Sec. 4.2) of
+ * accpot a against accpot r (device (N,4) arrays of the given precision):
+ * out (device uint64[3], overwritten) = { #(e_i > tol_a), #(e_i > tol_b),
+ * bit pattern of max e_i as an IEEE double }.  A zero reference acceleration
+ * counts as e_i = inf unless a_i is zero too.  Budgets on the median and the
+ * maximum follow from the counts: median <= tol_a iff 2 #(e > tol_a) <= N. */
+int etics_force_error(const void *a, const void *r, int64_t N, int precision, double tol_a,
+                      double tol_b, uint64_t *out, void *stream);
+
 /* Waits for `stream`, then returns and clears the device error word
  * (ETICS_OK if no kernel reported a data error since the last call). */
 int etics_get_error(void *stream);

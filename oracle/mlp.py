@@ -20,18 +20,23 @@ error entering a product are rounded to bf16; sums stay in FP64 here.  With
 ``quantize=False`` the whole network is FP64.
 
 Forecast features (``features``) and the forecast update (``advance``) are
-defined on a history of coefficient vectors c_0 .. c_7 (oldest first):
+defined on a history of coefficient vectors c_0 .. c_7 (oldest first) through
+its backward differences, each a single FP64 subtraction of the previous
+order: d1_k = c_k - c_{k-1}, d2_k = d1_k - d1_{k-1}, d3_k = d2_k - d2_{k-1},
+d4_k = d3_k - d3_{k-1}.  Eight blocks per coefficient:
 
-* block 0: (c_7 - mu) * inv_sigma                 (the state),
-* block 1: (c_7 - c_6) * inv_s1                    (the last first difference),
-* block 1+k, k = 1..6: ((c_{8-k} - c_{7-k}) - (c_{7-k} - c_{6-k})) * inv_s2
-  (the last six second differences, newest first),
+* block 0: (c_7 - mu) * inv_sigma                  (the state),
+* blocks 1, 2, 3: d1_7 * inv_s1, d2_7 * inv_s2, d3_7 * inv_s3,
+* blocks 4..7: d4_7, d4_6, d4_5, d4_4, each * inv_s4,
 
-each rounded to float32 and then to bf16 (both round-to-nearest-even).  The
-training target for a next vector c_8 is ((c_8 - c_7) - (c_7 - c_6)) * inv_s2
-rounded to float32: the change of the first difference, i.e. the correction
-to linear extrapolation.  ``advance`` inverts it:
-c_8 = (c_7 + (c_7 - c_6)) + s2 * y.  All FP64 operations are single roundings
+each rounded to float32 and then to bf16 (both round-to-nearest-even), laid
+out block-major in one row per history (the joint network sees every
+coefficient) or as one row of 8 per coefficient (a network shared by all
+coefficients).  The base forecast of c_8 is the cubic extrapolation
+P = ((c_7 + d1_7) + d2_7) + d3_7; the network learns what it misses, the
+next fourth difference: the training target for a next vector c_8 is
+d4_8 * inv_s4 rounded to float32 (d1_8 = c_8 - c_7 and so on), and
+``advance`` forms c_8 = P + s4 * y.  All FP64 operations are single roundings
 in the order written.
 
 Pins: ``tests/test_oracle_mlp.py`` (finite differences, closed forms of a
@@ -84,20 +89,6 @@ def unpack(params, dims):
         o += b
         out.append((w, bias))
     return out
-
-
-def init_params(dims, seed: int = 0) -> np.ndarray:
-    """Uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights, zero biases; the last
-    layer scaled by 0.1 so that the untrained network starts near zero."""
-    rng = np.random.Generator(np.random.Philox(key=seed))
-    p = np.zeros(param_count(dims))
-    o = 0
-    for i in range(len(dims) - 1):
-        a, b = dims[i], dims[i + 1]
-        lim = 1.0 / np.sqrt(a) * (0.1 if i == len(dims) - 2 else 1.0)
-        p[o:o + a * b] = rng.uniform(-lim, lim, a * b)
-        o += a * b + b
-    return p
 
 
 # ---------------------------------------------------------------------------
@@ -162,51 +153,75 @@ def adam(params, grads, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
 # forecast glue
 # ---------------------------------------------------------------------------
 HIST = 8
+NORM_ROWS = 7     # mu, inv_sigma, inv_s1, inv_s2, inv_s3, inv_s4, s4
+
+
+def _diff(c):
+    return c[1:] - c[:-1]
 
 
 def stats(traj):
-    """Normalisers of a coefficient trajectory (T x D, T >= 3): mean mu,
-    population standard deviation sigma, RMS first difference s1 and RMS second
-    difference s2 of every coefficient; inv_* = 1/s, or 0 where s == 0.
-    Returns (mu, inv_sigma, inv_s1, inv_s2, s2)."""
+    """Normalisers of a coefficient trajectory (T x D, T >= 5): mean mu,
+    population standard deviation sigma and the RMS s_k of the k-th backward
+    differences (k = 1..4) of every coefficient; inv_* = 1/s, or 0 where
+    s == 0.  Returns the NORM_ROWS x D array
+    (mu, inv_sigma, inv_s1, inv_s2, inv_s3, inv_s4, s4)."""
     c = np.asarray(traj, dtype=np.float64)
     mu = c.mean(axis=0)
     sigma = np.sqrt(((c - mu) ** 2).mean(axis=0))
-    d1 = c[1:] - c[:-1]
-    s1 = np.sqrt((d1 * d1).mean(axis=0))
-    d2 = d1[1:] - d1[:-1]
-    s2 = np.sqrt((d2 * d2).mean(axis=0))
 
     def inv(s):
         out = np.zeros_like(s)
         nz = s > 0
         out[nz] = 1.0 / s[nz]
         return out
-    return mu, inv(sigma), inv(s1), inv(s2), s2
+    rows = [mu, inv(sigma)]
+    d = c
+    for _ in range(4):
+        d = _diff(d)
+        s = np.sqrt((d * d).mean(axis=0))
+        rows.append(inv(s))
+    rows.append(s)
+    return np.stack(rows)
 
 
-def features(store, rows, mu, inv_sigma, inv_s1, inv_s2, next_rows=None):
-    """bf16 feature codes (B x 8D, uint16) of the histories store[rows[b]]
-    (rows: B x 8 indices, oldest first) and, with next_rows, float32 targets
+def _differences(c):
+    """Backward differences of a list of vectors: d[k][i] = k-th difference
+    ending at c[i] (defined for i >= k)."""
+    d = [list(c)]
+    for k in range(1, 5):
+        prev = d[k - 1]
+        d.append([None] * k + [prev[i] - prev[i - 1] for i in range(k, len(c))])
+    return d
+
+
+def features(store, rows, norm, next_rows=None, per_coeff=False):
+    """bf16 feature codes of the histories store[rows[b]] (rows: B x 8
+    indices, oldest first): B x 8D (block-major per row) or, per coefficient,
+    (B*D) x 8 (one row per coefficient); with next_rows, float32 targets
     (B x D)."""
     store = np.asarray(store, dtype=np.float64)
     rows = np.asarray(rows)
+    mu, isg, is1, is2, is3, is4, _ = norm
     bsz, d = rows.shape[0], store.shape[1]
     x = np.zeros((bsz, HIST * d), dtype=np.uint16)
     tgt = np.zeros((bsz, d), dtype=np.float32) if next_rows is not None else None
     for b in range(bsz):
         c = [store[rows[b, k]] for k in range(HIST)]
-        blocks = [(c[7] - mu) * inv_sigma, (c[7] - c[6]) * inv_s1]
-        for k in range(1, 7):
-            blocks.append(((c[8 - k] - c[7 - k]) - (c[7 - k] - c[6 - k])) * inv_s2)
+        dd = _differences(c)
+        blocks = [(c[7] - mu) * isg, dd[1][7] * is1, dd[2][7] * is2, dd[3][7] * is3]
+        for k in (7, 6, 5, 4):
+            blocks.append(dd[4][k] * is4)
         x[b] = bf16_bits(np.concatenate(blocks))
         if next_rows is not None:
-            c8 = store[next_rows[b]]
-            tgt[b] = (((c8 - c[7]) - (c[7] - c[6])) * inv_s2).astype(np.float32)
+            e = _differences(c + [store[next_rows[b]]])
+            tgt[b] = (e[4][8] * is4).astype(np.float32)
+    if per_coeff:
+        x = x.reshape(bsz, HIST, d).transpose(0, 2, 1).reshape(bsz * d, HIST).copy()
     return x, tgt
 
 
-def advance(ring, order, s2, y=None, coeffs=None):
+def advance(ring, order, norm, y=None, coeffs=None):
     """Forecast (y given) or push (coeffs given) the next coefficient vector
     into the ring of HIST vectors.  order: slots oldest..newest.  Returns
     (new ring, new order, the vector written)."""
@@ -215,7 +230,9 @@ def advance(ring, order, s2, y=None, coeffs=None):
     if coeffs is not None:
         new = np.asarray(coeffs, dtype=np.float64).copy()
     else:
-        c7, c6 = ring[order[7]], ring[order[6]]
-        new = (c7 + (c7 - c6)) + s2 * np.asarray(y, dtype=np.float32).astype(np.float64)
+        c = [ring[order[k]] for k in range(HIST)]
+        dd = _differences(c)
+        base = ((c[7] + dd[1][7]) + dd[2][7]) + dd[3][7]
+        new = base + norm[6] * np.asarray(y, dtype=np.float32).astype(np.float64)
     ring[order[0]] = new
     return ring, order[1:] + order[:1], new

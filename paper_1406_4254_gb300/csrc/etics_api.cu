@@ -210,6 +210,143 @@ int etics_leapfrog_step(void* posm, void* vel, void* accpot, int64_t N, double d
                  : etics::kick_f64(vel, accpot, N, dt, h.ctx);
 }
 
+int etics_leapfrog_step_coeffs(void* posm, void* vel, void* accpot, int64_t N, double dt,
+                               int n_max, int l_max, int precision, const double* coeffs,
+                               void* stream) {
+    if (!valid_n(N) || !valid_precision(precision) || !(dt == dt)) return ETICS_ERR_ARG;
+    if (n_max < 0 || l_max < 0 || !coeffs || !aligned(coeffs, 8)) return ETICS_ERR_ARG;
+    if (n_max > ETICS_NMAX_LIMIT || l_max > ETICS_LMAX_LIMIT) return ETICS_ERR_UNSUPPORTED;
+    if (check_particles(posm, N) || check_particles(vel, N) || check_particles(accpot, N))
+        return ETICS_ERR_ARG;
+    CtxHolder h;
+    int rc = make_ctx(stream, h);
+    if (rc) return rc;
+    const bool mixed = precision == ETICS_MIXED;
+    rc = mixed ? etics::kick_drift_f32(posm, vel, accpot, N, dt, h.ctx)
+               : etics::kick_drift_f64(posm, vel, accpot, N, dt, h.ctx);
+    if (rc) return rc;
+    rc = mixed ? etics::scf_field_f32(posm, N, n_max, l_max, coeffs, accpot, 3, h.ctx)
+               : etics::scf_field_f64(posm, N, n_max, l_max, coeffs, accpot, 3, h.ctx);
+    if (rc) return rc;
+    return mixed ? etics::kick_f32(vel, accpot, N, dt, h.ctx)
+                 : etics::kick_f64(vel, accpot, N, dt, h.ctx);
+}
+
+// ---- coefficient-forecasting MLP ---------------------------------------------
+namespace {
+bool mlp_args(const etics_mlp_shape* s, const float* params, const uint16_t* pb) {
+    return etics::mlp_param_count(s) > 0 && params && pb && aligned(params, 4) && aligned(pb, 2);
+}
+}  // namespace
+
+int64_t etics_mlp_param_count(const etics_mlp_shape* shape) {
+    return etics::mlp_param_count(shape);
+}
+
+size_t etics_mlp_workspace_bytes(const etics_mlp_shape* shape, int batch) {
+    return etics::mlp_workspace(shape, batch);
+}
+
+int etics_mlp_forward(const etics_mlp_shape* shape, const float* params,
+                      const uint16_t* params_bf16, const uint16_t* x, int batch, float* y,
+                      void* ws, size_t ws_bytes, void* stream) {
+    if (!mlp_args(shape, params, params_bf16) || batch < 0) return ETICS_ERR_ARG;
+    if (batch > 0 && (!x || !y || !ws || !aligned(x, 2) || !aligned(y, 4) || !aligned(ws, 256)))
+        return ETICS_ERR_ARG;
+    CtxHolder h;
+    const int rc = make_ctx(stream, h);
+    if (rc) return rc;
+    return etics::mlp_forward(shape, params, params_bf16, x, batch, y, ws, ws_bytes, h.ctx);
+}
+
+int etics_mlp_loss_grad(const etics_mlp_shape* shape, const float* params,
+                        const uint16_t* params_bf16, const uint16_t* x, const float* target,
+                        int batch, float* grads, double* loss, void* ws, size_t ws_bytes,
+                        void* stream) {
+    if (!mlp_args(shape, params, params_bf16) || batch < 1) return ETICS_ERR_ARG;
+    if (!x || !target || !grads || !loss || !ws || !aligned(x, 2) || !aligned(target, 4) ||
+        !aligned(grads, 4) || !aligned(loss, 8) || !aligned(ws, 256))
+        return ETICS_ERR_ARG;
+    CtxHolder h;
+    const int rc = make_ctx(stream, h);
+    if (rc) return rc;
+    return etics::mlp_loss_grad(shape, params, params_bf16, x, target, batch, grads, loss, ws,
+                                ws_bytes, h.ctx);
+}
+
+int etics_mlp_adam(const etics_mlp_shape* shape, float* params, const float* grads, float* m,
+                   float* v, int64_t t, float lr, float beta1, float beta2, float eps,
+                   uint16_t* params_bf16, void* stream) {
+    if (!mlp_args(shape, params, params_bf16) || !grads || !m || !v || t < 1) return ETICS_ERR_ARG;
+    if (!aligned(grads, 4) || !aligned(m, 4) || !aligned(v, 4)) return ETICS_ERR_ARG;
+    if (!(beta1 >= 0.0f && beta1 < 1.0f && beta2 >= 0.0f && beta2 < 1.0f && eps > 0.0f &&
+          lr == lr))
+        return ETICS_ERR_ARG;
+    CtxHolder h;
+    const int rc = make_ctx(stream, h);
+    if (rc) return rc;
+    return etics::mlp_adam(shape, params, grads, m, v, t, lr, beta1, beta2, eps, params_bf16,
+                           h.ctx);
+}
+
+int etics_mlp_to_bf16(const etics_mlp_shape* shape, const float* params, uint16_t* params_bf16,
+                      void* stream) {
+    if (!mlp_args(shape, params, params_bf16)) return ETICS_ERR_ARG;
+    CtxHolder h;
+    const int rc = make_ctx(stream, h);
+    if (rc) return rc;
+    return etics::mlp_to_bf16(shape, params, params_bf16, h.ctx);
+}
+
+int etics_coeff_stats(const double* traj, int T, int D, double* norm, void* stream) {
+    if (!traj || !norm || T < 5 || D < 1 || !aligned(traj, 8) || !aligned(norm, 8))
+        return ETICS_ERR_ARG;
+    CtxHolder h;
+    const int rc = make_ctx(stream, h);
+    if (rc) return rc;
+    return etics::coeff_stats(traj, T, D, norm, h.ctx);
+}
+
+int etics_coeff_features(const double* store, const int32_t* rows, const int32_t* next_rows,
+                         int batch, int D, const double* norm, int layout, uint16_t* x,
+                         float* target, void* stream) {
+    if (!store || !rows || !norm || !x || batch < 0 || D < 1 || (next_rows && !target))
+        return ETICS_ERR_ARG;
+    if (layout != ETICS_FEAT_JOINT && layout != ETICS_FEAT_PER_COEFF) return ETICS_ERR_ARG;
+    if (!aligned(store, 8) || !aligned(rows, 4) || !aligned(norm, 8) || !aligned(x, 2) ||
+        (next_rows && (!aligned(next_rows, 4) || !aligned(target, 4))))
+        return ETICS_ERR_ARG;
+    CtxHolder h;
+    const int rc = make_ctx(stream, h);
+    if (rc) return rc;
+    return etics::coeff_features(store, rows, next_rows, batch, D, norm,
+                                 layout == ETICS_FEAT_PER_COEFF, x, target, h.ctx);
+}
+
+int etics_coeff_advance(double* ring, int32_t* order, int D, const double* coeffs_in,
+                        const float* y, const double* norm, double* coeffs_out, int commit,
+                        void* stream) {
+    if (!ring || !order || D < 1 || (!coeffs_in == !y) || (y && !norm)) return ETICS_ERR_ARG;
+    if (!commit && !coeffs_out) return ETICS_ERR_ARG;
+    if (!aligned(ring, 8) || !aligned(order, 4) || (coeffs_in && !aligned(coeffs_in, 8)) ||
+        (y && !aligned(y, 4)) || (coeffs_out && !aligned(coeffs_out, 8)))
+        return ETICS_ERR_ARG;
+    CtxHolder h;
+    const int rc = make_ctx(stream, h);
+    if (rc) return rc;
+    return etics::coeff_advance(ring, order, D, coeffs_in, y, norm, coeffs_out, commit, h.ctx);
+}
+
+int etics_force_error(const void* a, const void* r, int64_t N, int precision, double tol_a,
+                      double tol_b, uint64_t* out, void* stream) {
+    if (!valid_n(N) || !valid_precision(precision) || !out || !aligned(out, 8)) return ETICS_ERR_ARG;
+    if (check_particles(a, N) || check_particles(r, N)) return ETICS_ERR_ARG;
+    CtxHolder h;
+    const int rc = make_ctx(stream, h);
+    if (rc) return rc;
+    return etics::force_error(a, r, N, precision, tol_a, tol_b, out, h.ctx);
+}
+
 int etics_scf_batch_plan(const etics_batch_item* items, int ninst,
                          const etics_batch_tuning* tuning, int precision, void* plan,
                          size_t plan_bytes, size_t* plan_bytes_needed, size_t* ws_bytes,

@@ -53,6 +53,29 @@ template <typename R>
 int batch_launch(const void* posm, const void* plan_host, const void* plan_dev, double* coeffs,
                  void* out, int out_mask, void* ws, size_t ws_bytes, const LaunchCtx& ctx);
 
+// ---- coefficient-forecasting MLP (etics_mlp.cu) ------------------------------
+int64_t mlp_param_count(const etics_mlp_shape* s);
+size_t mlp_workspace(const etics_mlp_shape* s, int batch);
+int mlp_forward(const etics_mlp_shape* s, const float* params, const uint16_t* params_bf16,
+                const uint16_t* x, int batch, float* y, void* ws, size_t ws_bytes,
+                const LaunchCtx& ctx);
+int mlp_loss_grad(const etics_mlp_shape* s, const float* params, const uint16_t* params_bf16,
+                  const uint16_t* x, const float* target, int batch, float* grads, double* loss,
+                  void* ws, size_t ws_bytes, const LaunchCtx& ctx);
+int mlp_adam(const etics_mlp_shape* s, float* params, const float* grads, float* m, float* v,
+             int64_t t, float lr, float beta1, float beta2, float eps, uint16_t* params_bf16,
+             const LaunchCtx& ctx);
+int mlp_to_bf16(const etics_mlp_shape* s, const float* params, uint16_t* params_bf16,
+                const LaunchCtx& ctx);
+int coeff_stats(const double* traj, int T, int D, double* norm, const LaunchCtx& ctx);
+int coeff_features(const double* store, const int32_t* rows, const int32_t* next, int batch, int D,
+                   const double* norm, int per_coeff, uint16_t* x, float* target,
+                   const LaunchCtx& ctx);
+int coeff_advance(double* ring, int32_t* order, int D, const double* coeffs_in, const float* y,
+                  const double* norm, double* coeffs_out, int commit, const LaunchCtx& ctx);
+int force_error(const void* a, const void* r, int64_t N, int precision, double tol_a,
+                double tol_b, uint64_t* out, const LaunchCtx& ctx);
+
 // ---- leapfrog (etics_step.cu) ----------------------------------------------
 int kick_drift_f32(void* posm, void* vel, const void* acc, int64_t N, double dt,
                    const LaunchCtx& ctx);

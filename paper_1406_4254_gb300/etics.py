@@ -33,6 +33,17 @@ _lib = None
 _ws_cache: dict = {}
 
 
+class MlpShape(ctypes.Structure):
+    _fields_ = [("nlayers", ctypes.c_int), ("dims", ctypes.c_int * 5)]
+
+    @classmethod
+    def of(cls, dims) -> "MlpShape":
+        dims = [int(d) for d in dims]
+        if not 2 <= len(dims) <= 5:
+            raise ValueError("an MLP has 1 to 4 layers")
+        return cls(len(dims) - 1, (ctypes.c_int * 5)(*(dims + [0] * (5 - len(dims)))))
+
+
 class EticsError(RuntimeError):
     def __init__(self, status: int, what: str):
         super().__init__(f"{what}: {_STATUS.get(status, 'unknown')} ({status})")
@@ -69,6 +80,21 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.etics_scf_batch.argtypes = [vp, vp, vp, i32, vp, vp, i32, vp, sz, vp]
         lib.etics_leapfrog_step.argtypes = [vp, vp, vp, i64, dbl, i32, i32, i32, i32, vp, vp, sz,
                                             vp]
+        lib.etics_leapfrog_step_coeffs.argtypes = [vp, vp, vp, i64, dbl, i32, i32, i32, vp, vp]
+        mp = ctypes.POINTER(MlpShape)
+        lib.etics_mlp_param_count.argtypes = [mp]
+        lib.etics_mlp_param_count.restype = i64
+        lib.etics_mlp_workspace_bytes.argtypes = [mp, i32]
+        lib.etics_mlp_workspace_bytes.restype = sz
+        lib.etics_mlp_forward.argtypes = [mp, vp, vp, vp, i32, vp, vp, sz, vp]
+        lib.etics_mlp_loss_grad.argtypes = [mp, vp, vp, vp, vp, i32, vp, vp, vp, sz, vp]
+        flt = ctypes.c_float
+        lib.etics_mlp_adam.argtypes = [mp, vp, vp, vp, vp, i64, flt, flt, flt, flt, vp, vp]
+        lib.etics_mlp_to_bf16.argtypes = [mp, vp, vp, vp]
+        lib.etics_coeff_stats.argtypes = [vp, i32, i32, vp, vp]
+        lib.etics_coeff_features.argtypes = [vp, vp, vp, i32, i32, vp, i32, vp, vp, vp]
+        lib.etics_coeff_advance.argtypes = [vp, vp, i32, vp, vp, vp, vp, i32, vp]
+        lib.etics_force_error.argtypes = [vp, vp, i64, i32, dbl, dbl, vp, vp]
         lib.etics_get_error.argtypes = [vp]
         lib.etics_strerror.argtypes = [i32]
         lib.etics_strerror.restype = ctypes.c_char_p
@@ -77,6 +103,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         for name in ("etics_scf_coeffs", "etics_scf_field", "etics_mex_field",
                      "etics_radial_sort", "etics_radial_keys", "etics_leapfrog_step",
                      "etics_scf_coeffs_noalloc", "etics_scf_batch_plan", "etics_scf_batch",
+                     "etics_leapfrog_step_coeffs", "etics_mlp_forward", "etics_mlp_loss_grad",
+                     "etics_mlp_adam", "etics_mlp_to_bf16", "etics_coeff_stats",
+                     "etics_coeff_features", "etics_coeff_advance", "etics_force_error",
                      "etics_get_error",
                      "etics_set_stage_events"):
             getattr(lib, name).restype = i32
@@ -251,6 +280,182 @@ def leapfrog_step(posm: torch.Tensor, vel: torch.Tensor, accpot: torch.Tensor, d
     _check(load().etics_leapfrog_step(posm.data_ptr(), vel.data_ptr(), accpot.data_ptr(), n,
                                       float(dt), method, n_max, l_max, prec, cp, wp, wb,
                                       _stream(stream)), "etics_leapfrog_step")
+
+
+def leapfrog_step_coeffs(posm: torch.Tensor, vel: torch.Tensor, accpot: torch.Tensor, dt: float,
+                         n_max: int, l_max: int, coeffs: torch.Tensor, stream=None) -> None:
+    """One in-place KDK step whose new force uses the given SCF coefficients."""
+    posm = _particles(posm, "posm")
+    vel = _particles(vel, "vel")
+    accpot = _particles(accpot, "accpot")
+    if vel.dtype != posm.dtype or accpot.dtype != posm.dtype:
+        raise TypeError("posm, vel and accpot must share a dtype")
+    _vector(coeffs, torch.float64, (n_max + 1) * (l_max + 1) ** 2, "coeffs")
+    _check(load().etics_leapfrog_step_coeffs(posm.data_ptr(), vel.data_ptr(), accpot.data_ptr(),
+                                             posm.shape[0], float(dt), n_max, l_max,
+                                             _precision(posm), coeffs.data_ptr(),
+                                             _stream(stream)), "etics_leapfrog_step_coeffs")
+
+
+# ---- coefficient-forecasting MLP ----------------------------------------------
+def _vector(t: torch.Tensor, dtype, numel: int | None, name: str) -> torch.Tensor:
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, has {t.numel()}")
+    return t
+
+
+def mlp_param_count(dims) -> int:
+    n = int(load().etics_mlp_param_count(ctypes.byref(MlpShape.of(dims))))
+    if n < 0:
+        raise EticsError(-1, "etics_mlp_param_count")
+    return n
+
+
+def mlp_workspace(dims, batch: int, device=None) -> torch.Tensor:
+    need = int(load().etics_mlp_workspace_bytes(ctypes.byref(MlpShape.of(dims)), int(batch)))
+    if need <= 0:
+        raise EticsError(-1, "etics_mlp_workspace_bytes")
+    return torch.empty(need + 256, dtype=torch.uint8, device=device or "cuda")
+
+
+def mlp_forward(dims, params: torch.Tensor, params_bf16: torch.Tensor, x: torch.Tensor,
+                y: torch.Tensor | None = None, ws: torch.Tensor | None = None,
+                stream=None) -> torch.Tensor:
+    """y = network(x); x: (batch, dims[0]) bfloat16, y: (batch, dims[-1]) float32."""
+    n = mlp_param_count(dims)
+    _vector(params, torch.float32, n, "params")
+    _vector(params_bf16, torch.bfloat16, n, "params_bf16")
+    _vector(x, torch.bfloat16, None, "x")
+    b = x.shape[0]
+    if x.numel() != b * dims[0]:
+        raise ValueError("x must be (batch, dims[0])")
+    if y is None:
+        y = torch.empty((b, dims[-1]), dtype=torch.float32, device=x.device)
+    _vector(y, torch.float32, b * dims[-1], "y")
+    if ws is None:
+        ws = mlp_workspace(dims, b, x.device)
+    wp, wb = _aligned_ptr(ws)
+    _check(load().etics_mlp_forward(ctypes.byref(MlpShape.of(dims)), params.data_ptr(),
+                                    params_bf16.data_ptr(), x.data_ptr(), b, y.data_ptr(), wp, wb,
+                                    _stream(stream)), "etics_mlp_forward")
+    return y
+
+
+def mlp_loss_grad(dims, params: torch.Tensor, params_bf16: torch.Tensor, x: torch.Tensor,
+                  target: torch.Tensor, grads: torch.Tensor, loss: torch.Tensor,
+                  ws: torch.Tensor | None = None, stream=None) -> None:
+    """loss (float64, 1 element) = MSE(network(x), target); grads = its gradient."""
+    n = mlp_param_count(dims)
+    _vector(params, torch.float32, n, "params")
+    _vector(params_bf16, torch.bfloat16, n, "params_bf16")
+    _vector(grads, torch.float32, n, "grads")
+    _vector(loss, torch.float64, 1, "loss")
+    _vector(x, torch.bfloat16, None, "x")
+    b = x.shape[0]
+    _vector(target, torch.float32, b * dims[-1], "target")
+    if ws is None:
+        ws = mlp_workspace(dims, b, x.device)
+    wp, wb = _aligned_ptr(ws)
+    _check(load().etics_mlp_loss_grad(ctypes.byref(MlpShape.of(dims)), params.data_ptr(),
+                                      params_bf16.data_ptr(), x.data_ptr(), target.data_ptr(), b,
+                                      grads.data_ptr(), loss.data_ptr(), wp, wb, _stream(stream)),
+           "etics_mlp_loss_grad")
+
+
+def mlp_adam(dims, params, grads, m, v, t: int, lr: float, params_bf16, beta1=0.9, beta2=0.999,
+             eps=1e-8, stream=None) -> None:
+    n = mlp_param_count(dims)
+    for name, tt in (("params", params), ("grads", grads), ("m", m), ("v", v)):
+        _vector(tt, torch.float32, n, name)
+    _vector(params_bf16, torch.bfloat16, n, "params_bf16")
+    _check(load().etics_mlp_adam(ctypes.byref(MlpShape.of(dims)), params.data_ptr(),
+                                 grads.data_ptr(), m.data_ptr(), v.data_ptr(), int(t), float(lr),
+                                 float(beta1), float(beta2), float(eps), params_bf16.data_ptr(),
+                                 _stream(stream)), "etics_mlp_adam")
+
+
+def mlp_to_bf16(dims, params, params_bf16, stream=None) -> None:
+    n = mlp_param_count(dims)
+    _vector(params, torch.float32, n, "params")
+    _vector(params_bf16, torch.bfloat16, n, "params_bf16")
+    _check(load().etics_mlp_to_bf16(ctypes.byref(MlpShape.of(dims)), params.data_ptr(),
+                                    params_bf16.data_ptr(), _stream(stream)), "etics_mlp_to_bf16")
+
+
+def coeff_stats(traj: torch.Tensor, norm: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """(7, D) normalisers of a (T, D) float64 coefficient trajectory."""
+    _vector(traj, torch.float64, None, "traj")
+    t, d = traj.shape
+    if norm is None:
+        norm = torch.empty((NORM_ROWS, d), dtype=torch.float64, device=traj.device)
+    _vector(norm, torch.float64, NORM_ROWS * d, "norm")
+    _check(load().etics_coeff_stats(traj.data_ptr(), t, d, norm.data_ptr(), _stream(stream)),
+           "etics_coeff_stats")
+    return norm
+
+
+FEAT_JOINT, FEAT_PER_COEFF = 0, 1
+NORM_ROWS = 7
+
+
+def coeff_features(store: torch.Tensor, rows: torch.Tensor, norm: torch.Tensor,
+                   next_rows: torch.Tensor | None = None, x: torch.Tensor | None = None,
+                   target: torch.Tensor | None = None, per_coeff: bool = False, stream=None):
+    """Network inputs of the histories store[rows] (rows: (batch, 8) int32,
+    oldest first): (batch, 8D) bfloat16 in the joint layout, (batch*D, 8) per
+    coefficient; with next_rows also the targets (batch, D) float32."""
+    _vector(store, torch.float64, None, "store")
+    _vector(rows, torch.int32, None, "rows")
+    d = store.shape[1]
+    b = rows.shape[0]
+    _vector(norm, torch.float64, NORM_ROWS * d, "norm")
+    if x is None:
+        shape = (b * d, 8) if per_coeff else (b, 8 * d)
+        x = torch.empty(shape, dtype=torch.bfloat16, device=store.device)
+    _vector(x, torch.bfloat16, b * 8 * d, "x")
+    np_ = tp = None
+    if next_rows is not None:
+        _vector(next_rows, torch.int32, b, "next_rows")
+        if target is None:
+            target = torch.empty((b, d), dtype=torch.float32, device=store.device)
+        _vector(target, torch.float32, b * d, "target")
+        np_, tp = next_rows.data_ptr(), target.data_ptr()
+    _check(load().etics_coeff_features(store.data_ptr(), rows.data_ptr(), np_, b, d,
+                                       norm.data_ptr(), FEAT_PER_COEFF if per_coeff else FEAT_JOINT,
+                                       x.data_ptr(), tp, _stream(stream)),
+           "etics_coeff_features")
+    return x, target
+
+
+def coeff_advance(ring: torch.Tensor, order: torch.Tensor, norm: torch.Tensor | None = None,
+                  coeffs_in: torch.Tensor | None = None, y: torch.Tensor | None = None,
+                  coeffs_out: torch.Tensor | None = None, commit: bool = True,
+                  stream=None) -> None:
+    _vector(ring, torch.float64, None, "ring")
+    _vector(order, torch.int32, 8, "order")
+    d = ring.shape[1]
+    ptr = lambda t: t.data_ptr() if t is not None else None  # noqa: E731
+    _check(load().etics_coeff_advance(ring.data_ptr(), order.data_ptr(), d, ptr(coeffs_in), ptr(y),
+                                      ptr(norm), ptr(coeffs_out), int(bool(commit)),
+                                      _stream(stream)), "etics_coeff_advance")
+
+
+def force_error(a: torch.Tensor, r: torch.Tensor, tol_a: float, tol_b: float,
+                out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Device int64[3]: #(e > tol_a), #(e > tol_b), bits of max e, for the
+    relative acceleration error e of accpot a against accpot r."""
+    a = _particles(a, "a")
+    r = _particles(r, "r")
+    if a.dtype != r.dtype or a.shape != r.shape:
+        raise ValueError("a and r must match")
+    if out is None:
+        out = torch.empty(3, dtype=torch.int64, device=a.device)
+    _check(load().etics_force_error(a.data_ptr(), r.data_ptr(), a.shape[0], _precision(a),
+                                    float(tol_a), float(tol_b), out.data_ptr(), _stream(stream)),
+           "etics_force_error")
+    return out
 
 
 class _BatchItem(ctypes.Structure):

@@ -7,6 +7,7 @@ import pytest
 import torch
 
 from oracle import mlp
+from paper_1406_4254_gb300 import inputs
 
 
 # ---------------------------------------------------------------------------
@@ -46,7 +47,7 @@ def test_bf16_matches_torch_cast():
 # ---------------------------------------------------------------------------
 def test_forward_matches_loops():
     dims = [3, 4, 2]
-    p = mlp.init_params(dims, seed=3)
+    p = inputs.mlp_params(dims, seed=3)
     p[mlp.param_count(dims) - 2:] = [0.25, -0.5]          # nonzero output bias
     x = np.array([[0.5, -1.0, 2.0], [0.0, 0.25, -0.75]])
     (w1, b1), (w2, b2) = mlp.unpack(p, dims)
@@ -61,7 +62,7 @@ def test_forward_matches_loops():
 def test_gradient_finite_differences():
     dims = [5, 4, 3, 2]
     rng = np.random.default_rng(0)
-    p = mlp.init_params(dims, seed=1) * 3.0
+    p = inputs.mlp_params(dims, seed=1) * 3.0
     p += rng.normal(size=p.size) * 0.1                   # nonzero biases too
     x = rng.normal(size=(3, 5))
     t = rng.normal(size=(3, 2))
@@ -106,7 +107,7 @@ def test_quantized_equals_exact_on_bf16_representable_data():
 def test_quantized_within_bf16_bound():
     dims = [16, 8, 4]
     rng = np.random.default_rng(4)
-    p = mlp.init_params(dims, seed=4)
+    p = inputs.mlp_params(dims, seed=4)
     x = mlp.bf16_round(rng.normal(size=(5, 16)))
     t = rng.normal(size=(5, 4))
     _, g0 = mlp.loss_grad(p, dims, x, t)
@@ -133,75 +134,109 @@ def test_adam_constant_gradient_closed_form():
 # ---------------------------------------------------------------------------
 # forecast features and update
 # ---------------------------------------------------------------------------
-def _poly_store(t0, nvec, a, b, c):
+def _poly_store(t0, nvec, coef):
+    """c_t = sum_k coef[k] t^k for t = t0 .. t0+nvec-1 (rows), exact in binary
+    for the dyadic coefficients and small t used here."""
     ts = np.arange(t0, t0 + nvec, dtype=np.float64)[:, None]
-    return a[None, :] + b[None, :] * ts + c[None, :] * ts * ts
+    return sum(coef[k][None, :] * ts ** k for k in range(len(coef)))
 
 
 def test_stats_closed_form():
     # c_t = a + b t (t = 0..T-1): mean a + b (T-1)/2, population variance
-    # b^2 (T^2 - 1)/12, RMS first difference |b|, second difference 0
+    # b^2 (T^2 - 1)/12, RMS first difference |b|, higher differences 0
     T = 9
     a = np.array([1.0, -2.0, 0.5])
     b = np.array([0.25, 0.0, -3.0])
-    mu, inv_sigma, inv_s1, inv_s2, s2 = mlp.stats(_poly_store(0, T, a, b, np.zeros(3)))
-    np.testing.assert_allclose(mu, a + b * (T - 1) / 2, rtol=1e-15)
+    norm = mlp.stats(_poly_store(0, T, [a, b]))
+    assert norm.shape == (mlp.NORM_ROWS, 3)
+    np.testing.assert_allclose(norm[0], a + b * (T - 1) / 2, rtol=1e-15)
     sig = np.abs(b) * np.sqrt((T * T - 1) / 12.0)
-    np.testing.assert_allclose(inv_sigma, np.where(sig > 0, 1 / np.where(sig > 0, sig, 1), 0), rtol=1e-14)
-    np.testing.assert_allclose(inv_s1, np.where(b != 0, 1 / np.where(b != 0, np.abs(b), 1), 0), rtol=1e-14)
-    assert np.all(inv_s2 == 0) and np.all(s2 == 0)
+    np.testing.assert_allclose(norm[1], np.where(sig > 0, 1 / np.where(sig > 0, sig, 1), 0), rtol=1e-14)
+    np.testing.assert_allclose(norm[2], np.where(b != 0, 1 / np.where(b != 0, np.abs(b), 1), 0), rtol=1e-14)
+    assert np.all(norm[3:] == 0)
 
 
-def test_features_of_quadratic_history():
-    # c_t = a + b t + c t^2: first difference b + c (2t - 1), every second
-    # difference 2c (exact in binary for these dyadic values)
+def test_stats_of_a_cubic():
+    # c_t = d t^3: third difference 6d everywhere, fourth difference 0
+    d = np.array([0.5, -0.125])
+    norm = mlp.stats(_poly_store(0, 12, [0 * d, 0 * d, 0 * d, d]))
+    np.testing.assert_allclose(norm[4], 1.0 / (6 * np.abs(d)), rtol=1e-15)
+    assert np.all(norm[5] == 0) and np.all(norm[6] == 0)
+
+
+def _norm(d, mu=0.5, isg=2.0, is1=4.0, is2=16.0, is3=0.5, is4=8.0, s4=0.125):
+    return np.array([[v] * d for v in (mu, isg, is1, is2, is3, is4, s4)], dtype=np.float64)
+
+
+def test_features_of_cubic_history():
+    # c_t = a + b t + c t^2 + e t^3: d1_t = b + c (2t-1) + e (3t^2-3t+1),
+    # d2_t = 2c + 6e (t-1), d3 = 6e, d4 = 0
     a = np.array([1.0, -0.5])
     b = np.array([0.25, 0.125])
     c = np.array([0.0625, -0.03125])
-    store = _poly_store(3, 9, a, b, c)          # t = 3..11
-    mu = np.array([0.5, 0.25])
-    inv_sigma = np.array([2.0, 0.5])
-    inv_s1 = np.array([4.0, 8.0])
-    inv_s2 = np.array([16.0, 2.0])
+    e = np.array([0.0078125, 0.015625])
+    store = _poly_store(3, 9, [a, b, c, e])     # t = 3..11
+    norm = _norm(2)
     rows = np.array([[0, 1, 2, 3, 4, 5, 6, 7]])
-    x, tgt = mlp.features(store, rows, mu, inv_sigma, inv_s1, inv_s2, next_rows=np.array([8]))
+    x, tgt = mlp.features(store, rows, norm, next_rows=np.array([8]))
     v = mlp.bf16_value(x[0]).reshape(8, 2)
     t7 = 10.0
-    np.testing.assert_array_equal(v[0], mlp.bf16_round((a + b * t7 + c * t7 * t7 - mu) * inv_sigma))
-    np.testing.assert_array_equal(v[1], mlp.bf16_round((b + c * (2 * t7 - 1)) * inv_s1))
-    for k in range(2, 8):
-        np.testing.assert_array_equal(v[k], 2 * c * inv_s2)
-    np.testing.assert_array_equal(tgt[0], (2 * c * inv_s2).astype(np.float32))
+    c7 = a + b * t7 + c * t7 ** 2 + e * t7 ** 3
+    np.testing.assert_array_equal(v[0], mlp.bf16_round((c7 - 0.5) * 2.0))
+    np.testing.assert_array_equal(v[1], mlp.bf16_round((b + c * (2 * t7 - 1) + e * (3 * t7 ** 2 - 3 * t7 + 1)) * 4.0))
+    np.testing.assert_array_equal(v[2], mlp.bf16_round((2 * c + 6 * e * (t7 - 1)) * 16.0))
+    np.testing.assert_array_equal(v[3], mlp.bf16_round(6 * e * 0.5))
+    assert np.all(v[4:] == 0) and np.all(tgt[0] == 0)
+    # one row of eight per coefficient: the same values, coefficient-major
+    xp, _ = mlp.features(store, rows, norm, per_coeff=True)
+    vp = mlp.bf16_value(xp)
+    assert vp.shape == (2, 8)
+    for j in range(2):
+        np.testing.assert_array_equal(vp[j], v[:, j])
+
+
+def test_features_fourth_differences_and_target():
+    # c_t = t^4 / 16: fourth difference 24/16 = 1.5 everywhere
+    q = np.array([1.0 / 16.0])
+    z = 0 * q
+    store = _poly_store(0, 9, [z, z, z, z, q])
+    x, tgt = mlp.features(store, np.arange(8)[None, :], _norm(1, is4=2.0),
+                          next_rows=np.array([8]))
+    v = mlp.bf16_value(x[0])
+    np.testing.assert_array_equal(v[4:], [3.0] * 4)
+    assert tgt[0, 0] == np.float32(3.0)
 
 
 def test_features_row_order_matters():
     rng = np.random.default_rng(8)
     store = rng.normal(size=(12, 5))
-    st = mlp.stats(store)
-    x1, _ = mlp.features(store, np.array([[0, 1, 2, 3, 4, 5, 6, 7]]), *st[:4])
-    x2, _ = mlp.features(store, np.array([[1, 0, 2, 3, 4, 5, 6, 7]]), *st[:4])
-    # swapping the two oldest vectors changes only the two oldest second
-    # differences (blocks 6 and 7: c_3-2c_2+c_1 and c_2-2c_1+c_0)
+    norm = mlp.stats(store)
+    x1, _ = mlp.features(store, np.array([[0, 1, 2, 3, 4, 5, 6, 7]]), norm)
+    x2, _ = mlp.features(store, np.array([[1, 0, 2, 3, 4, 5, 6, 7]]), norm)
+    # swapping the two oldest vectors changes only the fourth differences
+    # that reach back to c_1: d4_5 (block 6) and d4_4 (block 7)
     d = (x1[0] != x2[0]).reshape(8, 5).any(axis=1)
     assert list(d) == [False] * 6 + [True, True]
 
 
 def test_advance_inverts_target():
-    # forecasting with the exact target reproduces the next quadratic vector;
-    # s2 and inv_s2 are powers of two so that s2 * y undoes the scaling exactly
-    a = np.array([1.0, -0.5, 0.0])
-    b = np.array([0.25, 0.125, -1.0])
-    c = np.array([0.0625, -0.03125, 0.5])
-    store = _poly_store(0, 9, a, b, c)
-    inv_s2 = np.array([4.0, 0.5, 1.0])
-    s2 = 1.0 / inv_s2
-    _, tgt = mlp.features(store, np.arange(8)[None, :], np.zeros(3), np.ones(3), np.ones(3),
-                          inv_s2, next_rows=np.array([8]))
+    # forecasting with the exact target reproduces the next vector of a
+    # quartic history (the cubic base misses exactly d4 = 24 q); s4 and
+    # inv_s4 are powers of two so that s4 * y undoes the scaling exactly
+    coef = [np.array([1.0, -0.5, 0.0]), np.array([0.25, 0.125, -1.0]),
+            np.array([0.0625, -0.03125, 0.5]), np.array([0.0, 0.5, -0.25]),
+            np.array([0.125, 0.0, 0.0625])]
+    store = _poly_store(0, 9, coef)
+    norm = _norm(3, is4=4.0, s4=0.25)
+    _, tgt = mlp.features(store, np.arange(8)[None, :], norm, next_rows=np.array([8]))
     ring = store[:8].copy()
     order = list(range(8))
-    ring2, order2, new = mlp.advance(ring, order, s2, y=tgt[0])
+    ring2, order2, new = mlp.advance(ring, order, norm, y=tgt[0])
     np.testing.assert_array_equal(new, store[8])
     assert order2 == [1, 2, 3, 4, 5, 6, 7, 0] and np.array_equal(ring2[0], store[8])
+    # with y = 0 the forecast is the cubic extrapolation 4c7 - 6c6 + 4c5 - c4
+    _, _, base = mlp.advance(ring, order, norm, y=np.zeros(3))
+    np.testing.assert_array_equal(base, 4 * store[7] - 6 * store[6] + 4 * store[5] - store[4])
     # pushing a given vector writes it into the oldest slot
-    ring3, order3, _ = mlp.advance(ring2, order2, s2, coeffs=np.array([7.0, 8.0, 9.0]))
+    ring3, order3, _ = mlp.advance(ring2, order2, norm, coeffs=np.array([7.0, 8.0, 9.0]))
     assert order3 == [2, 3, 4, 5, 6, 7, 0, 1] and np.array_equal(ring3[1], [7.0, 8.0, 9.0])
