@@ -171,6 +171,23 @@ class RawEvents:
         return float(out.value)
 
 
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """The largest of one float over all ranks (the slowest replica sets the
+    job's time); x itself with no process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job throughput: the units every replica processed over the
+    slowest replica's time."""
+    return units_per_rank * world / (ms * 1e-3)
+
+
 # --- GPU arm -------------------------------------------------------------------
 def run_etics(args, rank, world):
     import torch
@@ -249,12 +266,8 @@ def run_etics(args, rank, world):
     clk = clocks.stop()
     launches = etics.launch_count() - l0
     etics.check_error()
-    ms = statistics.mean(times)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = 2 * n * world / (ms * 1e-3)
+    ms = max_over_ranks(statistics.mean(times), dist, dev)
+    value = job_throughput(2 * n, world, ms)
 
     # ---- e2e: host (pinned) buffers through the public API ------------------
     host_in = torch.tensor(pm, dtype=torch.float32).pin_memory()
@@ -281,11 +294,7 @@ def run_etics(args, rank, world):
         t_end.record(stream)
         torch.cuda.synchronize()
         e2e_t.append(t_start.elapsed_time(t_end))
-    e2e_ms = statistics.mean(e2e_t)
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(statistics.mean(e2e_t), dist, dev)
 
     # ---- FP64 GPU path (same particles), a few steps -------------------------
     ws64s = etics.workspace(n, N_MAX, L_MAX, etics.SCF, etics.FP64, dev)
@@ -792,7 +801,7 @@ def main():
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms"],
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic", "config": cfg, "roofline": roof,
-           "e2e": {"value": 2 * n * world / (res["e2e_ms"] * 1e-3), "unit": UNIT,
+           "e2e": {"value": job_throughput(2 * n, world, res["e2e_ms"]), "unit": UNIT,
                    "h2d_bytes_per_step": n * 16, "d2h_bytes_per_step": 2 * n * 16},
            "gpu_launches": res["launches"], "clocks": res["clocks"],
            "stages_ms": {k: round(v, 5) for k, v in st.items()},
