@@ -333,7 +333,7 @@ def run_etics(args, rank, world):
 
 
 def accuracy(pm, out_scf, out_mex, sample=4096):
-    """eps~ of eq. 18 of the mixed path against the FP64 oracle at the same
+    """eps~ of eq. 23 of the mixed path against the FP64 oracle at the same
     (FP32-rounded) positions: SCF coefficients from all particles and field on
     a sample; MEX on all particles."""
     import oracle
@@ -383,7 +383,7 @@ def run_leapfrog(args):
     kick-drift-kick steps at dt = 0.01 (the paper's integrator, Secs. 3.4 and
     5.4), each step one CUDA-graph replay of etics_leapfrog_step.  Reports the
     energy drift |dE/E0| of the mixed and FP64 paths and, every 10th step, the
-    relative force error (eq. 18) of the mixed path against the FP64 oracle at
+    relative force error (eq. 23) of the mixed path against the FP64 oracle at
     the same positions (oracle coefficients from all particles, field on a
     16384-particle sample)."""
     import torch

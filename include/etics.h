@@ -6,9 +6,9 @@
  * (Sec. 2.1, eqs. 1-3) is the Poisson equation of N point masses with G = 1;
  * the library returns the acceleration a = -grad(Phi) and the potential Phi at
  * every particle by one of two expansions:
- *   SCF (Sec. 2.3 eq. 16, Sec. 2.4, Sec. 3.3): coefficients of the
+ *   SCF (Sec. 2.4 eq. 18, Sec. 2.5, Sec. 3.3): coefficients of the
  *       Hernquist-Ostriker basis, then a field pass over the coefficients;
- *   MEX (Sec. 2.3 eqs. 13-15, Sec. 2.2, Sec. 3.2): radial sort, then inner and
+ *   MEX (Sec. 2.4 eqs. 15-17, Sec. 2.2, Sec. 3.2): radial sort, then inner and
  *       outer cumulative multipole sums along radius.
  *
  * Conventions shared by every entry point
@@ -75,7 +75,7 @@ enum etics_out { ETICS_OUT_ACC = 1, ETICS_OUT_POT = 2 };   /* force/potential/bo
  * device.  Returns 0 for invalid arguments. */
 size_t etics_workspace_bytes(int64_t N, int n_max, int l_max, int method, int precision);
 
-/* SCF coefficient pass (Sec. 3.3, first part; eq. 16):
+/* SCF coefficient pass (Sec. 3.3, first part; eq. 18):
  *   c[n][l,m] = (1/J_nl) sum_k m_k phi_nl(r_k) Y_lm(x_k),
  *   J_nl = int rho_nl phi_nl r^2 dr.
  * coeffs: device double[(n_max+1)*(l_max+1)^2], overwritten.  ws: device
@@ -91,7 +91,7 @@ int etics_scf_coeffs(const void *posm, int64_t N, int n_max, int l_max, int prec
 int etics_scf_field(const void *posm, int64_t N, int n_max, int l_max, int precision,
                     const double *coeffs, void *accpot, int out_mask, void *stream);
 
-/* MEX force calculation (Sec. 2.3 eqs. 13-15, Sec. 3.2): radial sort, inner
+/* MEX force calculation (Sec. 2.4 eqs. 15-17, Sec. 3.2): radial sort, inner
  * and outer exclusive cumulative sums of m r^l Y_lm and m r^-(l+1) Y_lm, and
  * Phi_i = -sum_l 4pi/(2l+1) sum_m [q_lm(i) r^-(l+1) + p_lm(i) r^l] Y_lm(x_i).
  * The order is by r^2 = (x*x + y*y) + z*z evaluated in FP64 (bitwise as a

@@ -10,9 +10,9 @@ Citations are to the paper's sections and equations (Meiron, Li,
 Holley-Bockelmann & Spurzem, "Expansion Techniques for Collisionless Stellar
 Dynamical Simulations"):
 
-* ``scf_coeffs`` / ``scf_field``: Sec. 2.3 eq. 16 with the Hernquist-Ostriker
-  radial basis of Sec. 2.4 (two passes of Sec. 3.3).
-* ``mex_field``: Sec. 2.3 eqs. 13-15 with the sorted cumulative sums of
+* ``scf_coeffs`` / ``scf_field``: Sec. 2.4 eq. 18 with the Hernquist-Ostriker
+  radial basis of Sec. 2.5 (two passes of Sec. 3.3).
+* ``mex_field``: Sec. 2.4 eqs. 15-17 with the sorted cumulative sums of
   Sec. 2.2 and Sec. 3.2.
 * ``direct``: Sec. 2.1 eq. 4.
 * ``leapfrog_step``: the kick-drift-kick step mentioned in Secs. 3.4 and 5.4.
@@ -101,7 +101,7 @@ def default_threads() -> int:
 
 
 def phi_nl(n: int, l: int, r: float):
-    """Radial potential basis phi_nl(r) and d phi_nl/dr (Sec. 2.4)."""
+    """Radial potential basis phi_nl(r) and d phi_nl/dr (Sec. 2.5)."""
     lib = _load()
     a, b = ctypes.c_double(), ctypes.c_double()
     _check(lib.etics_ref_phi_nl(n, l, float(r), ctypes.byref(a), ctypes.byref(b)), "phi_nl")
@@ -109,7 +109,7 @@ def phi_nl(n: int, l: int, r: float):
 
 
 def jnl(n: int, l: int) -> float:
-    """Normalisation integral of rho_nl * phi_nl * r^2 (Sec. 2.4 basis)."""
+    """Normalisation integral of rho_nl * phi_nl * r^2 (Sec. 2.5 basis)."""
     return float(_load().etics_ref_jnl(n, l))
 
 
@@ -121,7 +121,7 @@ def ylm(l_max: int, x: float, y: float, z: float) -> np.ndarray:
 
 
 def scf_coeffs(pos, mass, n_max: int, l_max: int) -> np.ndarray:
-    """SCF coefficients c[n, l*l+l+m] (Sec. 2.3 eq. 16), shape (n_max+1, (l_max+1)^2)."""
+    """SCF coefficients c[n, l*l+l+m] (Sec. 2.4 eq. 18), shape (n_max+1, (l_max+1)^2)."""
     p = _pos(pos)
     m = np.ascontiguousarray(mass, dtype=np.float64)
     out = np.zeros((n_max + 1, (l_max + 1) ** 2))
@@ -144,7 +144,7 @@ def scf_field(pos, n_max: int, l_max: int, coeffs, nthreads: int = 0):
 
 
 def mex_field(pos, mass, l_max: int):
-    """MEX acceleration, potential and the radial order (Sec. 2.3 eqs. 13-15)."""
+    """MEX acceleration, potential and the radial order (Sec. 2.4 eqs. 15-17)."""
     p = _pos(pos)
     m = np.ascontiguousarray(mass, dtype=np.float64)
     acc = np.zeros((len(p), 3))

@@ -36,7 +36,7 @@ static void gegenbauer_all(int n, double alpha, double x, double *C)
                 - (k + 2.0 * alpha - 2.0) * C[k - 2]) / k;
 }
 
-/* Hernquist-Ostriker potential basis (Sec. 2.4; HO92 construction with the
+/* Hernquist-Ostriker potential basis (Sec. 2.5; HO92 construction with the
  * Hernquist model as zeroth order, scale length a = 1):
  *   phi_nl(r) = - r^l / (1+r)^(2l+1) * C_n^(2l+3/2)(xi),  xi = (r-1)/(r+1).
  * Its radial derivative uses d/dxi C_n^alpha = 2 alpha C_{n-1}^(alpha+1) and
@@ -362,7 +362,7 @@ static int key_cmp(const void *a, const void *b)
     return (x->idx < y->idx) ? -1 : (x->idx > y->idx);
 }
 
-/* MEX (Sec. 2.3 eqs. 13-15):
+/* MEX (Sec. 2.4 eqs. 15-17):
  *   Phi(r_i) = - sum_l 4pi/(2l+1) sum_m [q_lm(i) r_i^-(l+1) + p_lm(i) r_i^l] Y_lm(i)
  *   q_lm(i)  = sum_{j before i} m_j r_j^l      Y_lm(j)
  *   p_lm(i)  = sum_{j after i}  m_j r_j^-(l+1) Y_lm(j)

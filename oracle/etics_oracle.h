@@ -31,7 +31,7 @@
 extern "C" {
 #endif
 
-/* Hernquist-Ostriker radial potential basis function (Sec. 2.4, HO92 basis):
+/* Hernquist-Ostriker radial potential basis function (Sec. 2.5, HO92 basis):
  * phi = -r^l (1+r)^-(2l+1) C_n^(2l+3/2)(xi), xi = (r-1)/(r+1); dphi = d phi/dr. */
 int etics_ref_phi_nl(int n, int l, double r, double *phi, double *dphi);
 
@@ -42,20 +42,20 @@ double etics_ref_jnl(int n, int l);
  * l <= l_max, written to Y[l*l+l+m].  At the origin theta = phi = 0. */
 int etics_ref_ylm(int l_max, double x, double y, double z, double *Y);
 
-/* SCF coefficients (Sec. 2.3 eq. 16, Sec. 3.3 step 1):
+/* SCF coefficients (Sec. 2.4 eq. 18, Sec. 3.3 step 1):
  *   c[n][j] = (1/J_nl) sum_k m_k phi_nl(r_k) Y_j(theta_k, phi_k)
  * summed serially in particle order. */
 int etics_ref_scf_coeffs(const double *pos, const double *mass, long n_part,
                          int n_max, int l_max, double *coeffs);
 
-/* SCF field at arbitrary points (Sec. 2.3 eq. 16, Sec. 3.3 step 2):
+/* SCF field at arbitrary points (Sec. 2.4 eq. 18, Sec. 3.3 step 2):
  *   Phi = sum c[n][j] phi_nl(r) Y_j,   acc = -grad Phi.
  * acc or pot may be NULL.  nthreads <= 0 uses all online cores. */
 int etics_ref_scf_field(const double *pos, long n_part, int n_max, int l_max,
                         const double *coeffs, double *acc, double *pot,
                         int nthreads);
 
-/* MEX field at the particles themselves (Sec. 2.3 eqs. 13-15, Sec. 2.2):
+/* MEX field at the particles themselves (Sec. 2.4 eqs. 15-17, Sec. 2.2):
  * particles ordered by r^2 = (x*x + y*y) + z*z in FP64, ties by index;
  * q_lm(i) sums the particles strictly before i, p_lm(i) strictly after.
  * order (nullable) receives the sorted particle indices. */

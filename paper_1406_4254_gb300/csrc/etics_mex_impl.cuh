@@ -1,7 +1,7 @@
 // etics_mex_impl.cuh -- MEX kernels after the radial sort (templated on the
 // arithmetic type; instantiated in etics_mex_f32.cu / etics_mex_f64.cu).
 //
-// Method (paper Sec. 2.3 eqs. 13-15, the sorted cumulative sums of Sec. 2.2):
+// Method (paper Sec. 2.4 eqs. 15-17, the sorted cumulative sums of Sec. 2.2):
 //   q_lm(i) = sum_{j before i} m_j r_j^l Y_lm(j),  p_lm(i) = sum_{j after i} m_j r_j^-(l+1) Y_lm(j)
 //   Phi_i   = -sum_l 4pi/(2l+1) sum_m [q_lm(i) r_i^-(l+1) + p_lm(i) r_i^l] Y_lm(i)
 // and a_i = -grad Phi_i at fixed q, p.

@@ -6,7 +6,7 @@
 // memory.  The radial basis of the bin's levels is evaluated by the lane
 // itself (Gegenbauer recursion with immediate constants), so there is no
 // per-tile cross-thread reduction and no padding work.  Method as in
-// etics_scf_impl.cuh (paper Sec. 2.3 eq. 16, Sec. 2.4 basis).
+// etics_scf_impl.cuh (paper Sec. 2.4 eq. 18, Sec. 2.5 basis).
 #pragma once
 
 #include "etics_scf_impl.cuh"

@@ -2,7 +2,7 @@
 // arithmetic type; instantiated for float in etics_scf_f32.cu and for double
 // in etics_scf_f64.cu).
 //
-// Method (paper Sec. 2.3 eq. 16, basis of Sec. 2.4, two passes of Sec. 3.3):
+// Method (paper Sec. 2.4 eq. 18, basis of Sec. 2.5, two passes of Sec. 3.3):
 //   c_nlm = (1/J_nl) sum_k m_k phi_nl(r_k) Y_lm(x_k)             (coefficients)
 //   Phi   = sum c_nlm phi_nl(r) Y_lm,  a = -grad Phi              (field)
 //   phi_nl = -r^l (1+r)^-(2l+1) C_n^(2l+3/2)(xi),  xi = (r-1)/(r+1).

@@ -7,7 +7,7 @@ from paper_1406_4254_gb300 import inputs
 DTYPES = {"mixed": torch.float32, "fp64": torch.float64}
 
 # tolerances on the relative acceleration error eps_i = |a - a_ref| / |a_ref|
-# (the paper's eq. 18): FP64 path vs oracle, and the mixed path's stated bound
+# (the paper's eq. 23): FP64 path vs oracle, and the mixed path's stated bound
 TOL = {"fp64": {"median": 1e-13, "max": 1e-10},
        "mixed": {"median": 1e-5, "max": 1e-4}}
 

@@ -1,7 +1,7 @@
 """Pins of the FP64 oracle's MEX, direct-summation and leapfrog functions, and
 of the input samplers.
 
-MEX is Sec. 2.3 eqs. 13-15 of the paper (with the sorted exclusive cumulative
+MEX is Sec. 2.4 eqs. 15-17 of the paper (with the sorted exclusive cumulative
 sums of Sec. 2.2); direct summation is Sec. 2.1 eq. 4.
 """
 import math
@@ -51,7 +51,8 @@ def test_mex_monopole_is_shell_theorem():
 def test_mex_converges_to_direct_summation_geometric_radii():
     """For radii r_j = 2^(j-16) every pair has r_</r_> <= 1/2, so the
     multipole series of 1/|x-x'| converges like 2^-l: at l_max = 40 MEX equals
-    direct summation (Sec. 2.3, MEX 'is similar to direct methods')."""
+    direct summation (Sec. 2.4: the MEX potential at a particle is built from the
+    individual inner and outer particles, as in direct summation)."""
     rng = np.random.default_rng(7)
     n = 33
     r = 2.0 ** (np.arange(n) - 16.0)

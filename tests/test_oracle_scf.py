@@ -3,8 +3,8 @@ come from the oracle itself (scipy's Gegenbauer polynomials and spherical
 harmonics, closed-form Hernquist and Plummer potentials, exact quadrature,
 rotation invariance, finite differences).
 
-SCF is Sec. 2.3 eq. 16 of the paper with the Hernquist-Ostriker radial basis
-it adopts in Sec. 2.4.
+SCF is Sec. 2.4 eq. 18 of the paper with the Hernquist-Ostriker radial basis
+it adopts in Sec. 2.5.
 """
 import math
 
@@ -77,7 +77,7 @@ def test_jnl_closed_form_and_quadrature():
 def test_phi_nl_matches_scipy_and_poisson(n, l):
     """phi_nl against scipy's Gegenbauer, its derivative against finite
     differences, and the radial Poisson equation
-    phi'' + 2 phi'/r - l(l+1) phi / r^2 = 4 pi rho_nl (Sec. 2.4)."""
+    phi'' + 2 phi'/r - l(l+1) phi / r^2 = 4 pi rho_nl (Sec. 2.5)."""
     for r in [0.03, 0.3, 1.0, 2.7, 11.0]:
         p, dp = oracle.phi_nl(n, l, r)
         assert p == pytest.approx(phi_nl_scipy(n, l, r), rel=1e-12, abs=1e-300)
@@ -118,7 +118,7 @@ def test_ylm_matches_scipy_real_harmonics():
                                     (7, 4, -3), (2, 6, 0), (9, 5, -5)])
 def test_biorthogonality_by_exact_quadrature(target):
     """Quadrature 'particles' whose masses sample rho_n'l' Y_l'm' (scipy) give
-    c_nlm = delta_nn' delta_ll' delta_mm' (Sec. 2.3: coefficients are the
+    c_nlm = delta_nn' delta_ll' delta_mm' (Sec. 2.5: coefficients are the
     projections of the density on the biorthogonal basis)."""
     n1, l1, m1 = target
     pos, R, TH, PH, W = quadrature(40, 16, 32)

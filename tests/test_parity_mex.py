@@ -1,8 +1,8 @@
 """GPU MEX (radix sort + scans + field through the C ABI) against the FP64
-oracle (paper Sec. 2.3 eqs. 13-15 with the sort of Sec. 2.2).
+oracle (paper Sec. 2.4 eqs. 15-17 with the sort of Sec. 2.2).
 
 The radial order is integer work and must match bit for bit; fields are
-compared per particle with eq. 18's relative error."""
+compared per particle with eq. 23's relative error."""
 import numpy as np
 import pytest
 import torch
@@ -102,7 +102,7 @@ def test_field_matches_oracle(precision, l_max):
     etics.check_error()
     o = out.cpu().numpy()
     # the innermost particle has no inner mass: its force is pure noise of the
-    # outer moments; compare all particles with the eq. 18 metric
+    # outer moments; compare all particles with the eq. 23 metric
     assert_field_close(o, acc_ref, pot_ref, precision, f"mex l={l_max}")
 
 

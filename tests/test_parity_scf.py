@@ -1,7 +1,7 @@
 """GPU SCF (CUDA kernels through the C ABI) against the FP64 oracle.
 
-Coefficients (paper Sec. 2.3 eq. 16) element by element; accelerations and
-potentials per particle with the relative error of eq. 18, at sizes that span
+Coefficients (paper Sec. 2.4 eq. 18) element by element; accelerations and
+potentials per particle with the relative error of eq. 23, at sizes that span
 many tiles with a ragged tail, at the benchmark's full size (N = 2^20,
 (n_max, l_max) = (10, 6)), and on edge cases.
 """
