@@ -22,6 +22,7 @@
 #include <cmath>
 
 #include "etics_internal.h"
+#include "etics_tc.cuh"
 
 namespace etics {
 
@@ -409,19 +410,25 @@ __global__ void force_error_kernel(const Vec4<R>* __restrict__ a, const Vec4<R>*
 }
 
 // ---- host planning ---------------------------------------------------------
-struct GemmShape { int M, N, K, splits, kslice; };
+// A product runs on the tcgen05 kernel (128 x 128 tiles, K step 64) when both
+// output dimensions fill a tile at least half, else on the mma.sync kernel
+// (64 x 64 tiles, K step 32).  Split-K brings the block count near two per SM
+// while keeping >= 4 (mma.sync) or >= 2 (tcgen05) K steps per slice.
+struct GemmShape { int M, N, K, splits, kslice; bool tc; };
 
 GemmShape gemm_shape(int M, int N, int K) {
-    GemmShape s{M, N, K, 1, 0};
-    const int tiles = ((M + kBM - 1) / kBM) * ((N + kBN - 1) / kBN);
-    const int ktiles = (K + kBK - 1) / kBK;
+    GemmShape s{M, N, K, 1, 0, M >= 64 && N >= 64};
+    const int bm = s.tc ? tc::kM : kBM, bn = s.tc ? tc::kN : kBN, bk = s.tc ? tc::kK : kBK;
+    const int tiles = ((M + bm - 1) / bm) * ((N + bn - 1) / bn);
+    const int ktiles = (K + bk - 1) / bk;
     int splits = (kTargetBlocks + tiles - 1) / tiles;
-    const int max_splits = ktiles / 4 > 1 ? ktiles / 4 : 1;   // >= 4 K tiles per slice
+    const int min_steps = s.tc ? 2 : 4;
+    const int max_splits = ktiles / min_steps > 1 ? ktiles / min_steps : 1;
     if (splits > max_splits) splits = max_splits;
     if (splits > 64) splits = 64;
     if (splits < 1) splits = 1;
     const int per = (ktiles + splits - 1) / splits;
-    s.kslice = per * kBK;
+    s.kslice = per * bk;
     s.splits = (ktiles + per - 1) / per;
     return s;
 }
@@ -506,9 +513,19 @@ int gemm(const bf16* A, int64_t lda, const bf16* Bm, int64_t ldb, int M, int N, 
          const float* bias, int act, const float* h, float* out, bf16* out_b,
          const LaunchCtx& ctx) {
     const GemmShape s = gemm_shape(M, N, K);
-    dim3 grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM, s.splits);
-    mlp_gemm_kernel<TA, TB><<<grid, kGemmThreads, 0, ctx.stream>>>(A, lda, Bm, ldb, part, M, N, K,
-                                                                  s.kslice);
+    if (s.tc) {
+        auto k = tc::gemm_kernel<TA, TB>;
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tc::kSmemBytes))
+            return ETICS_ERR_CUDA;
+        dim3 grid((N + tc::kN - 1) / tc::kN, (M + tc::kM - 1) / tc::kM, s.splits);
+        k<<<grid, tc::kThreads, tc::kSmemBytes, ctx.stream>>>(A, lda, Bm, ldb, part, M, N, K,
+                                                              s.kslice, ctx.err);
+    } else {
+        dim3 grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM, s.splits);
+        mlp_gemm_kernel<TA, TB><<<grid, kGemmThreads, 0, ctx.stream>>>(A, lda, Bm, ldb, part, M,
+                                                                      N, K, s.kslice);
+    }
     if (cudaGetLastError()) return ETICS_ERR_CUDA;
     mlp_epilogue_kernel<<<grid_1d((int64_t)M * N, ctx), 256, 0, ctx.stream>>>(
         part, s.splits, M, N, bias, act, h, out, out_b);

@@ -35,10 +35,14 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
-SHAPES = [([40, 24, 13], 5),                # one tile, ragged everything
-          ([96, 72, 40, 19], 37),           # several tiles, odd widths
+# products with an output side below 64 run on the mma.sync kernel, the
+# others on the tcgen05 kernel (128 x 128 tiles)
+SHAPES = [([40, 24, 13], 5),                # one tile, ragged everything (mma.sync)
+          ([96, 72, 40, 19], 37),           # several tiles, odd widths (mma.sync)
+          ([512, 384, 200], 300),           # tcgen05: 3 x 3 tiles, ragged, split-K
+          ([8, 256, 256, 1], 2000),         # the shared per-coefficient network
           ([1080, 256, 256, 135], 100),     # split-K in the first layer
-          ([9720, 256, 256, 1215], 64)]     # the (14, 8) forecaster's shape
+          ([9720, 256, 256, 1215], 64)]     # the joint (14, 8) forecaster's shape
 
 
 @pytest.mark.parametrize("dims,batch", SHAPES)
