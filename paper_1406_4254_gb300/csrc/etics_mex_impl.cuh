@@ -10,13 +10,14 @@
 //   pass 1  gathers the particles in radial order (sorted copy), and reduces
 //           each tile's moments m rho^l Y and m rho^-(l+1) Y (rho = r / s_t,
 //           s_t a power of two per tile, so FP32 never overflows) to FP64.
+//           It also stores each thread's sums over its kMexP particles.
 //   carry   scans the per-tile FP64 sums in a fixed order: exclusive forward
 //           for the inner moments, exclusive reverse (a true suffix sum) for
 //           the outer ones -- deterministic.
-//   pass 2  recomputes the moments, scans them inside the tile (warp
-//           shuffles + shared memory, forward and reverse), evaluates the
-//           field at every particle from the exclusive q and p, and scatters
-//           (a, Phi) back to the caller's order.
+//   pass 2  scans those thread sums inside the tile (warp shuffles + shared
+//           memory, forward and reverse), evaluates the field at every
+//           particle from the exclusive q and p in a forward and a reverse
+//           sweep, and scatters (a, Phi) back to the caller's order.
 // All harmonics are the unnormalised Cartesian solid harmonics of
 // etics_common.cuh; the MEX weights (l-m)!/(l+m)! (x2 for m > 0) restore the
 // orthonormal normalisation and the 4pi/(2l+1) factor at once.
@@ -213,7 +214,7 @@ template <typename R>
 __global__ void __launch_bounds__(kMexThreads)
 mex_pass1_kernel(const Vec4<R>* __restrict__ posm, const uint32_t* __restrict__ perm, int64_t N,
                  int l_max, Vec4<R>* __restrict__ sorted, double* __restrict__ tile_agg,
-                 unsigned* err) {
+                 R* __restrict__ thread_sums, unsigned* err) {
     __shared__ Vec4<R> s_pt[kMexTile];
     __shared__ R s_red[kMexThreads / 32][2 * kMexNC];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -256,6 +257,16 @@ mex_pass1_kernel(const Vec4<R>* __restrict__ posm, const uint32_t* __restrict__ 
         MexParticle<R> pt;
         pt.init(s_pt[k * kMexThreads + tid], scale);
         particle_moments<R>(pt, l_max, ain, aout);
+    }
+    // this thread's inner and outer sums for pass 2 (component-major, so the
+    // stores of a warp are contiguous)
+    {
+        R* ts = thread_sums + (size_t)blockIdx.x * 2 * kMexNC * kMexThreads + tid;
+#pragma unroll
+        for (int c = 0; c < kMexNC; ++c) {
+            ts[(size_t)c * kMexThreads] = ain[c];
+            ts[(size_t)(kMexNC + c) * kMexThreads] = aout[c];
+        }
     }
 #pragma unroll
     for (int c = 0; c < kMexNC; ++c) {
@@ -324,8 +335,8 @@ mex_carry_kernel(const double* __restrict__ tile_agg, int ntiles, double* __rest
 template <typename R, bool ACC>
 __global__ void __launch_bounds__(kMexThreads, 4)
 mex_pass2_kernel(const Vec4<R>* __restrict__ sorted, const uint32_t* __restrict__ perm, int64_t N,
-                 int l_max, const double* __restrict__ carry, Vec4<R>* __restrict__ out,
-                 int out_mask, unsigned* err) {
+                 int l_max, const double* __restrict__ carry, const R* __restrict__ thread_sums,
+                 Vec4<R>* __restrict__ out, int out_mask, unsigned* err) {
     constexpr int NW = kMexThreads / 32;
     __shared__ Vec4<R> s_pt[kMexTile];
     __shared__ Vec4<R> s_f[kMexTile];   // inner part of each particle's field
@@ -335,13 +346,25 @@ mex_pass2_kernel(const Vec4<R>* __restrict__ sorted, const uint32_t* __restrict_
     const int64_t base = (int64_t)blockIdx.x * kMexTile;
     const int64_t rem = N - base;
     const int nt = (int)(rem < kMexTile ? rem : kMexTile);
+    // thread sums of the inner and outer moments of its kMexP particles, as
+    // pass 1 computed them (same particles, order and rounding); loaded first
+    // so that their latency overlaps the staging below
+    R a[kMexNC], b[kMexNC];
+    {
+        const R* ts = thread_sums + (size_t)blockIdx.x * 2 * kMexNC * kMexThreads + tid;
+#pragma unroll
+        for (int c = 0; c < kMexNC; ++c) {
+            a[c] = ts[(size_t)c * kMexThreads];
+            b[c] = ts[(size_t)(kMexNC + c) * kMexThreads];
+        }
+    }
     for (int i = tid; i < kMexTile; i += kMexThreads)
         st4(&s_pt[mex_slot(i)], i < nt ? ld4(sorted + base + i) : mk4<R>(R(0), R(0), R(0), R(0)));
     __syncthreads();
     int e;
     {
-        const Vec4<R> a = s_pt[mex_slot(0)], b = s_pt[mex_slot(nt - 1)];
-        e = tile_exponent<R>(radius<R>(a.x, a.y, a.z), radius<R>(b.x, b.y, b.z));
+        const Vec4<R> pa = s_pt[mex_slot(0)], pb = s_pt[mex_slot(nt - 1)];
+        e = tile_exponent<R>(radius<R>(pa.x, pa.y, pa.z), radius<R>(pb.x, pb.y, pb.z));
     }
     const R scale = ldexp(R(1), -e);
     for (int c = tid; c < 2 * kMexNC; c += kMexThreads) {
@@ -351,16 +374,6 @@ mex_pass2_kernel(const Vec4<R>* __restrict__ sorted, const uint32_t* __restrict_
         const double v = carry[(size_t)blockIdx.x * 2 * kMexNC + c];
         if (c < kMexNC) s_q0[cc] = (R)ldexp(v, -l * e);
         else s_p0[cc] = (R)ldexp(v, (l + 1) * e);
-    }
-    // thread sums of the inner and outer moments of its kMexP particles
-    R a[kMexNC], b[kMexNC];
-#pragma unroll
-    for (int c = 0; c < kMexNC; ++c) { a[c] = R(0); b[c] = R(0); }
-#pragma unroll 1
-    for (int k = 0; k < kMexP; ++k) {
-        MexParticle<R> pt;
-        pt.init(s_pt[k * kMexThreads + tid], scale);
-        particle_moments<R>(pt, l_max, a, b);
     }
     // inner sums: exclusive prefix before this thread; outer sums: exclusive
     // suffix after it (a true suffix sum, never total minus prefix)
@@ -434,6 +447,7 @@ struct MexBuffers {
     Vec4<R>* sorted;
     double* tile_agg;
     double* carry;
+    R* thread_sums;      // [tile][2 * kMexNC][kMexThreads]
 };
 
 template <typename R>
@@ -452,6 +466,7 @@ inline MexBuffers<R> mex_buffers(void* ws, int64_t N, size_t* total) {
     b.sorted = reinterpret_cast<Vec4<R>*>(take(n * sizeof(Vec4<R>)));
     b.tile_agg = reinterpret_cast<double*>(take(nt * 2 * kMexNC * sizeof(double)));
     b.carry = reinterpret_cast<double*>(take(nt * 2 * kMexNC * sizeof(double)));
+    b.thread_sums = reinterpret_cast<R*>(take(nt * 2 * kMexNC * kMexThreads * sizeof(R)));
     if (total) *total = off;
     return b;
 }
@@ -475,7 +490,7 @@ inline int mex_field_impl(const void* posm, int64_t N, int l_max, void* out, int
     const int nt = mex_tiles(N);
     const Vec4<R>* pp = reinterpret_cast<const Vec4<R>*>(posm);
     mex_pass1_kernel<R><<<nt, kMexThreads, 0, ctx.stream>>>(pp, b.sort.vals_a, N, l_max, b.sorted,
-                                                            b.tile_agg, ctx.err);
+                                                            b.tile_agg, b.thread_sums, ctx.err);
     if (cudaGetLastError()) return ETICS_ERR_CUDA;
     ++*ctx.launches;
     stage_event(ctx, 3);
@@ -486,10 +501,10 @@ inline int mex_field_impl(const void* posm, int64_t N, int l_max, void* out, int
     Vec4<R>* op = reinterpret_cast<Vec4<R>*>(out);
     if (out_mask & ETICS_OUT_ACC)
         mex_pass2_kernel<R, true><<<nt, kMexThreads, 0, ctx.stream>>>(
-            b.sorted, b.sort.vals_a, N, l_max, b.carry, op, out_mask, ctx.err);
+            b.sorted, b.sort.vals_a, N, l_max, b.carry, b.thread_sums, op, out_mask, ctx.err);
     else
         mex_pass2_kernel<R, false><<<nt, kMexThreads, 0, ctx.stream>>>(
-            b.sorted, b.sort.vals_a, N, l_max, b.carry, op, out_mask, ctx.err);
+            b.sorted, b.sort.vals_a, N, l_max, b.carry, b.thread_sums, op, out_mask, ctx.err);
     if (cudaGetLastError()) return ETICS_ERR_CUDA;
     ++*ctx.launches;
     stage_event(ctx, 5);
