@@ -363,32 +363,35 @@ def run_etics(args, rank, world):
         result = {"ms": ms, "value": value, "stage": {k: statistics.mean(v) for k, v in stage.items()},
                   "launches": launches, "clocks": clk, "e2e_ms": e2e_ms, "serial_ms": serial_ms,
                   "f64": (statistics.mean(f64_scf), statistics.mean(f64_mex)),
-                  "out_scf": out_scf, "out_mex": out_mex, "pm": pm}
+                  "out_scf": out_scf, "out_mex": out_mex, "x": x}
     if dist:
         dist.barrier()
         dist.destroy_process_group()
     return result
 
 
-def accuracy(pm, out_scf, out_mex, sample=4096):
-    """eps~ of eq. 23 of the mixed path against the FP64 oracle at the same
-    (FP32-rounded) positions: SCF coefficients from all particles and field on
-    a sample; MEX on all particles."""
-    import oracle
-    ref = pm.astype(np.float32).astype(np.float64)
-    c = oracle.scf_coeffs(ref[:, :3], ref[:, 3], N_MAX, L_MAX)
-    idx = np.random.default_rng(0).choice(len(pm), min(sample, len(pm)), replace=False)
-    a_ref, _ = oracle.scf_field(ref[idx, :3], N_MAX, L_MAX, c)
-    a = out_scf.cpu().numpy()[idx, :3]
-    es = np.linalg.norm(a - a_ref, axis=1) / np.linalg.norm(a_ref, axis=1)
-    a_ref, _, _ = oracle.mex_field(ref[:, :3], ref[:, 3], L_MAX)
-    a = out_mex.cpu().numpy()[:, :3]
-    em = np.linalg.norm(a - a_ref, axis=1) / np.linalg.norm(a_ref, axis=1)
+def accuracy(x, out_scf, out_mex):
+    """eps~ of eq. 23 (single against double precision of the same method) of
+    the mixed path: the library's FP64 path at the same (FP32-rounded)
+    positions is the reference; the parity tests tie that path to the FP64
+    oracle to 1e-13."""
+    from paper_1406_4254_gb300 import etics
+    xr = x.double()
+    c = etics.scf_coeffs(xr, N_MAX, L_MAX)
+    a_scf = etics.scf_field(xr, c, N_MAX, L_MAX)
+    a_mex = etics.mex_field(xr, L_MAX)
+    etics.check_error()
+
+    def eps(a, r):
+        a = a.double().cpu().numpy()[:, :3]
+        r = r.cpu().numpy()[:, :3]
+        return np.linalg.norm(a - r, axis=1) / np.linalg.norm(r, axis=1)
 
     def st(e):
         return {"median": float(np.median(e)), "p99": float(np.quantile(e, 0.99)),
-                "max": float(e.max())}
-    return {"scf": st(es) | {"sample": len(idx)}, "mex": st(em) | {"sample": len(pm)}}
+                "max": float(e.max()), "sample": int(len(e))}
+    return {"reference": "FP64 GPU path at the same positions",
+            "scf": st(eps(out_scf, a_scf)), "mex": st(eps(out_mex, a_mex))}
 
 
 def oracle_step_time(pm_sample):
@@ -421,11 +424,10 @@ def run_leapfrog(args):
     kick-drift-kick steps at dt = 0.01 (the paper's integrator, Secs. 3.4 and
     5.4), each step one CUDA-graph replay of etics_leapfrog_step.  Reports the
     energy drift |dE/E0| of the mixed and FP64 paths and, every 10th step, the
-    relative force error (eq. 23) of the mixed path against the FP64 oracle at
-    the same positions (oracle coefficients from all particles, field on a
-    16384-particle sample)."""
+    relative force error (eq. 23) of the mixed path against the library's
+    FP64 path at the same positions (coefficients from all particles, field
+    on a 16384-particle sample)."""
     import torch
-    import oracle
     from paper_1406_4254_gb300 import etics, inputs
     dev = torch.device("cuda", 0)
     n = args.n
@@ -469,11 +471,13 @@ def run_leapfrog(args):
             torch.cuda.synchronize()
             times.append(t0.elapsed_time(t1))
             if label == "mixed" and step % check_every == 0 and not args.no_accuracy:
-                xp = x.double().cpu().numpy()
-                c = oracle.scf_coeffs(xp[:, :3], xp[:, 3], N_MAX, L_MAX)
-                idx = np.random.default_rng(step).choice(n, 16384, replace=False)
-                a_ref, _ = oracle.scf_field(xp[idx, :3], N_MAX, L_MAX, c)
-                a = acc.double().cpu().numpy()[idx, :3]
+                xp = x.double()
+                c = etics.scf_coeffs(xp, N_MAX, L_MAX)
+                idx = torch.tensor(np.random.default_rng(step).choice(n, 16384, replace=False),
+                                   device=dev)
+                a_ref = etics.scf_field(xp[idx].contiguous(), c, N_MAX, L_MAX)
+                a_ref = a_ref.cpu().numpy()[:, :3]
+                a = acc.double()[idx].cpu().numpy()[:, :3]
                 e = np.linalg.norm(a - a_ref, axis=1) / np.linalg.norm(a_ref, axis=1)
                 errs.append({"step": step, "median": float(np.median(e)),
                              "p99": float(np.quantile(e, 0.99)), "max": float(e.max())})
@@ -483,7 +487,7 @@ def run_leapfrog(args):
         res[label] = {"ms_per_step": ms, "particle_steps_per_s": n / (ms * 1e-3),
                       "energy_drift": abs(e1 / e0 - 1.0), "E0": e0, "E_end": e1}
         if errs:
-            res[label]["force_error_vs_oracle"] = errs
+            res[label]["force_error_vs_fp64"] = errs
     return {"experiment": "leapfrog", "workload": f"plummer b=1 N={n} SCF(10,6) "
             f"{steps} KDK steps dt={dt}, graph-captured step", **res}
 
@@ -733,6 +737,81 @@ def run_surrogate(args):
             "plain_mixed_split_ms": {"coefficients": ms_coef, "field": ms_field}}
 
 
+def run_accuracy(args):
+    """Sec. 4.1's study: the relative force error eps_i = |F_i - F_real| / |F_real|
+    (eq. 22) of MEX and SCF against the smooth force of the model the
+    particles were drawn from, in FP64 as the paper did.  Models: the Ferrers
+    n = 1 ellipsoids model1 (10:10:9) and model2 (3:2:1) of the paper, with
+    their polynomial potential recomputed from the 1-D index-symbol
+    integrals, and the closed-form Hernquist and Plummer spheres.  N from
+    10^3 to 10^6; realisations are stacked up to 10^6 particles per point (at
+    most 100).  MEX at l_max = 0, 2, 4, 6; SCF at l_max = 6 with n_max =
+    0..14 and at l_max = 10 with n_max = 6, 10, 14 (the paper's Fig. 8 sweep,
+    where SCF approaches MEX as n_max grows).  The overlap of the log10(eps)
+    histograms of SCF and MEX at l_max = 6 measures that approach."""
+    import torch
+    from paper_1406_4254_gb300 import etics, inputs, models
+    dev = torch.device("cuda", 0)
+    co = {"model1": models.ferrers_coefficients(models.MODEL1),
+          "model2": models.ferrers_coefficients(models.MODEL2)}
+
+    def sample(model, n, seed):
+        if model in ("model1", "model2"):
+            axes = models.MODEL1 if model == "model1" else models.MODEL2
+            pm = models.ferrers(n, seed=seed, axes=axes)
+            acc, _ = models.ferrers_force(pm[:, :3], axes, co[model])
+        elif model == "hernquist":
+            pm = inputs.hernquist(n, seed=seed)
+            acc, _ = models.hernquist_force(pm[:, :3])
+        else:
+            pm, _ = inputs.plummer(n, seed=seed)
+            acc, _ = models.plummer_force(pm[:, :3])
+        return pm, acc
+
+    methods = ([("mex", 0, l) for l in (0, 2, 4, 6)] +
+               [("scf", n, 6) for n in (0, 2, 4, 6, 10, 14)] +
+               [("scf", n, 10) for n in (6, 10, 14)])
+    bins = np.linspace(-9.0, 1.0, 101)
+    out = {}
+    for model in ("model1", "model2", "hernquist", "plummer"):
+        out[model] = {}
+        for n in args.acc_n:
+            reps = max(1, min(100, 1000000 // n))
+            errs = {m: [] for m in methods}
+            for rep in range(reps):
+                pm, a_real = sample(model, n, 1000 * rep + 17)
+                x = torch.tensor(pm, dtype=torch.float64, device=dev)
+                nr = np.linalg.norm(a_real, axis=1)
+                for meth in methods:
+                    kind, nm, lm = meth
+                    if kind == "mex":
+                        a = etics.mex_field(x, lm)
+                    else:
+                        a, _ = etics.scf_force(x, nm, lm)
+                    a = a.cpu().numpy()[:, :3]
+                    errs[meth].append(np.linalg.norm(a - a_real, axis=1) / nr)
+            etics.check_error()
+            row = {}
+            hist = {}
+            for meth, es in errs.items():
+                e = np.concatenate(es)
+                key = f"mex_l{meth[2]}" if meth[0] == "mex" else f"scf_n{meth[1]}_l{meth[2]}"
+                row[key] = {"mean": float(e.mean()), "median": float(np.median(e)),
+                            "p90": float(np.quantile(e, 0.9))}
+                h, _ = np.histogram(np.log10(np.maximum(e, 1e-12)), bins=bins)
+                hist[key] = h / max(1, h.sum())
+            row["overlap_with_mex_l6"] = {k: float(np.minimum(hist[k], hist["mex_l6"]).sum())
+                                          for k in hist if k.startswith("scf") and k.endswith("_l6")}
+            row["realisations"] = reps
+            out[model][str(n)] = row
+    return {"experiment": "accuracy", "precision": "FP64",
+            "error": "eps_i = |F_i - F_real| / |F_real| (eq. 22); mean, median and p90 over "
+                     "all particles of all realisations",
+            "models": {"model1": "Ferrers n=1, axes 10:10:9", "model2": "Ferrers n=1, axes 3:2:1",
+                       "hernquist": "Hernquist a=1", "plummer": "Plummer b=1"},
+            "results": out}
+
+
 def emit(obj):
     print(json.dumps(obj), flush=True)
 
@@ -748,7 +827,9 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=65536)
-    ap.add_argument("--experiment", choices=["leapfrog", "batch", "surrogate"], default=None)
+    ap.add_argument("--experiment", choices=["leapfrog", "batch", "surrogate", "accuracy"],
+                    default=None)
+    ap.add_argument("--acc-n", type=int, nargs="+", default=[1000, 10000, 100000, 1000000])
     ap.add_argument("--lf-steps", type=int, default=100)
     ap.add_argument("--sur-n", type=int, default=1 << 26)
     ap.add_argument("--sur-steps", type=int, default=2000)
@@ -757,6 +838,9 @@ def main():
     args = ap.parse_args()
     if args.experiment == "surrogate":
         emit(run_surrogate(args))
+        return
+    if args.experiment == "accuracy":
+        emit(run_accuracy(args))
         return
     if args.experiment == "leapfrog":
         emit(run_leapfrog(args))
@@ -856,7 +940,7 @@ def main():
            "mixed_per_method": {"scf_particle_forces_per_s": n / (st["scf"] * 1e-3),
                                 "mex_particle_forces_per_s": n / (st["mex"] * 1e-3)}}
     if not args.no_accuracy:
-        out["accuracy_eps_vs_oracle"] = accuracy(res["pm"], res["out_scf"], res["out_mex"])
+        out["accuracy_eps_mixed_vs_fp64"] = accuracy(res["x"], res["out_scf"], res["out_mex"])
     if not args.no_cpu_baseline and world >= 1:
         out["cpu_baseline"] = cpu_baseline(args.cpu_sample, 3)
     emit(out)

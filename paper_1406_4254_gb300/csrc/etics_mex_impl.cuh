@@ -346,25 +346,13 @@ mex_pass2_kernel(const Vec4<R>* __restrict__ sorted, const uint32_t* __restrict_
     const int64_t base = (int64_t)blockIdx.x * kMexTile;
     const int64_t rem = N - base;
     const int nt = (int)(rem < kMexTile ? rem : kMexTile);
-    // thread sums of the inner and outer moments of its kMexP particles, as
-    // pass 1 computed them (same particles, order and rounding); loaded first
-    // so that their latency overlaps the staging below
-    R a[kMexNC], b[kMexNC];
-    {
-        const R* ts = thread_sums + (size_t)blockIdx.x * 2 * kMexNC * kMexThreads + tid;
-#pragma unroll
-        for (int c = 0; c < kMexNC; ++c) {
-            a[c] = ts[(size_t)c * kMexThreads];
-            b[c] = ts[(size_t)(kMexNC + c) * kMexThreads];
-        }
-    }
     for (int i = tid; i < kMexTile; i += kMexThreads)
         st4(&s_pt[mex_slot(i)], i < nt ? ld4(sorted + base + i) : mk4<R>(R(0), R(0), R(0), R(0)));
     __syncthreads();
     int e;
     {
-        const Vec4<R> pa = s_pt[mex_slot(0)], pb = s_pt[mex_slot(nt - 1)];
-        e = tile_exponent<R>(radius<R>(pa.x, pa.y, pa.z), radius<R>(pb.x, pb.y, pb.z));
+        const Vec4<R> a = s_pt[mex_slot(0)], b = s_pt[mex_slot(nt - 1)];
+        e = tile_exponent<R>(radius<R>(a.x, a.y, a.z), radius<R>(b.x, b.y, b.z));
     }
     const R scale = ldexp(R(1), -e);
     for (int c = tid; c < 2 * kMexNC; c += kMexThreads) {
@@ -374,6 +362,17 @@ mex_pass2_kernel(const Vec4<R>* __restrict__ sorted, const uint32_t* __restrict_
         const double v = carry[(size_t)blockIdx.x * 2 * kMexNC + c];
         if (c < kMexNC) s_q0[cc] = (R)ldexp(v, -l * e);
         else s_p0[cc] = (R)ldexp(v, (l + 1) * e);
+    }
+    // thread sums of the inner and outer moments of its kMexP particles, as
+    // pass 1 computed them (same particles, order and rounding)
+    R a[kMexNC], b[kMexNC];
+    {
+        const R* ts = thread_sums + (size_t)blockIdx.x * 2 * kMexNC * kMexThreads + tid;
+#pragma unroll
+        for (int c = 0; c < kMexNC; ++c) {
+            a[c] = ts[(size_t)c * kMexThreads];
+            b[c] = ts[(size_t)(kMexNC + c) * kMexThreads];
+        }
     }
     // inner sums: exclusive prefix before this thread; outer sums: exclusive
     // suffix after it (a true suffix sum, never total minus prefix)
