@@ -11,7 +11,8 @@ Holley-Bockelmann & Spurzem, "Expansion Techniques for Collisionless Stellar
 Dynamical Simulations"):
 
 * ``scf_coeffs`` / ``scf_field``: Sec. 2.4 eq. 18 with the Hernquist-Ostriker
-  radial basis of Sec. 2.5 (two passes of Sec. 3.3).
+  radial basis of Sec. 2.5 (two passes of Sec. 3.3), or with the
+  Clutton-Brock basis Sec. 2.5 names (``basis=CB``).
 * ``mex_field``: Sec. 2.4 eqs. 15-17 with the sorted cumulative sums of
   Sec. 2.2 and Sec. 3.2.
 * ``direct``: Sec. 2.1 eq. 4.
@@ -76,6 +77,11 @@ def _load():
         lib.etics_ref_leapfrog_step.argtypes = [dp, dp, dp, dp, dp, c_long, c_double,
                                                 c_int, c_int, c_int, dp, c_int]
         lib.etics_ref_default_threads.restype = c_int
+        lib.etics_ref_phi_nl_b.argtypes = [c_int, c_int, c_int, c_double, dp, dp]
+        lib.etics_ref_jnl_b.argtypes = [c_int, c_int, c_int]
+        lib.etics_ref_jnl_b.restype = c_double
+        lib.etics_ref_scf_coeffs_b.argtypes = [c_int, dp, dp, c_long, c_int, c_int, dp]
+        lib.etics_ref_scf_field_b.argtypes = [c_int, dp, c_long, c_int, c_int, dp, dp, dp, c_int]
         _lib = lib
         return lib
 
@@ -100,17 +106,21 @@ def default_threads() -> int:
     return int(_load().etics_ref_default_threads())
 
 
-def phi_nl(n: int, l: int, r: float):
+HO, CB = 0, 1     # radial bases of Sec. 2.5: Hernquist-Ostriker, Clutton-Brock
+
+
+def phi_nl(n: int, l: int, r: float, basis: int = HO):
     """Radial potential basis phi_nl(r) and d phi_nl/dr (Sec. 2.5)."""
     lib = _load()
     a, b = ctypes.c_double(), ctypes.c_double()
-    _check(lib.etics_ref_phi_nl(n, l, float(r), ctypes.byref(a), ctypes.byref(b)), "phi_nl")
+    _check(lib.etics_ref_phi_nl_b(basis, n, l, float(r), ctypes.byref(a), ctypes.byref(b)),
+           "phi_nl")
     return a.value, b.value
 
 
-def jnl(n: int, l: int) -> float:
+def jnl(n: int, l: int, basis: int = HO) -> float:
     """Normalisation integral of rho_nl * phi_nl * r^2 (Sec. 2.5 basis)."""
-    return float(_load().etics_ref_jnl(n, l))
+    return float(_load().etics_ref_jnl_b(basis, n, l))
 
 
 def ylm(l_max: int, x: float, y: float, z: float) -> np.ndarray:
@@ -120,17 +130,17 @@ def ylm(l_max: int, x: float, y: float, z: float) -> np.ndarray:
     return out
 
 
-def scf_coeffs(pos, mass, n_max: int, l_max: int) -> np.ndarray:
+def scf_coeffs(pos, mass, n_max: int, l_max: int, basis: int = HO) -> np.ndarray:
     """SCF coefficients c[n, l*l+l+m] (Sec. 2.4 eq. 18), shape (n_max+1, (l_max+1)^2)."""
     p = _pos(pos)
     m = np.ascontiguousarray(mass, dtype=np.float64)
     out = np.zeros((n_max + 1, (l_max + 1) ** 2))
-    _check(_load().etics_ref_scf_coeffs(_dp(p), _dp(m), len(p), n_max, l_max, _dp(out)),
-           "scf_coeffs")
+    _check(_load().etics_ref_scf_coeffs_b(basis, _dp(p), _dp(m), len(p), n_max, l_max,
+                                          _dp(out)), "scf_coeffs")
     return out
 
 
-def scf_field(pos, n_max: int, l_max: int, coeffs, nthreads: int = 0):
+def scf_field(pos, n_max: int, l_max: int, coeffs, nthreads: int = 0, basis: int = HO):
     """SCF acceleration (N,3) and potential (N,) at arbitrary points."""
     p = _pos(pos)
     c = np.ascontiguousarray(coeffs, dtype=np.float64)
@@ -138,8 +148,8 @@ def scf_field(pos, n_max: int, l_max: int, coeffs, nthreads: int = 0):
         raise ValueError("coefficient shape mismatch")
     acc = np.zeros((len(p), 3))
     pot = np.zeros(len(p))
-    _check(_load().etics_ref_scf_field(_dp(p), len(p), n_max, l_max, _dp(c), _dp(acc),
-                                       _dp(pot), int(nthreads)), "scf_field")
+    _check(_load().etics_ref_scf_field_b(basis, _dp(p), len(p), n_max, l_max, _dp(c),
+                                         _dp(acc), _dp(pot), int(nthreads)), "scf_field")
     return acc, pot
 
 

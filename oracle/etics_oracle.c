@@ -36,57 +36,103 @@ static void gegenbauer_all(int n, double alpha, double x, double *C)
                 - (k + 2.0 * alpha - 2.0) * C[k - 2]) / k;
 }
 
-/* Hernquist-Ostriker potential basis (Sec. 2.5; HO92 construction with the
- * Hernquist model as zeroth order, scale length a = 1):
- *   phi_nl(r) = - r^l / (1+r)^(2l+1) * C_n^(2l+3/2)(xi),  xi = (r-1)/(r+1).
- * Its radial derivative uses d/dxi C_n^alpha = 2 alpha C_{n-1}^(alpha+1) and
- * dxi/dr = 2/(1+r)^2.  Fills phi[0..n_max] (and dphi if non-NULL). */
-static void radial_all(int n_max, int l, double r, double *phi, double *dphi)
+/* Radial potential bases (Sec. 2.5), scale length 1.
+ *
+ * basis 0, Hernquist-Ostriker (HO92; the Hernquist model is the zeroth term):
+ *   phi_nl(r) = - r^l / (1+r)^(2l+1) * C_n^(2l+3/2)(xi),  xi = (r-1)/(r+1),
+ *   dxi/dr = 2/(1+r)^2.
+ * basis 1, Clutton-Brock (CB73; the Plummer model is the zeroth term):
+ *   phi_nl(r) = - r^l / (1+r^2)^(l+1/2) * C_n^(l+1)(xi),  xi = (r^2-1)/(r^2+1),
+ *   dxi/dr = 4r/(1+r^2)^2.
+ * Radial derivatives use d/dxi C_n^alpha = 2 alpha C_{n-1}^(alpha+1).  Fills
+ * phi[0..n_max] (and dphi if non-NULL). */
+static double basis_alpha(int basis, int l)
 {
-    double alpha = 2.0 * l + 1.5;
-    double xi = (r - 1.0) / (r + 1.0);
-    double C[64], Cp[64];
-    gegenbauer_all(n_max, alpha, xi, C);
+    return basis == 0 ? 2.0 * l + 1.5 : l + 1.0;
+}
+
+static void radial_all_b(int basis, int n_max, int l, double r, double *phi, double *dphi)
+{
+    double alpha = basis_alpha(basis, l);
+    double xi, f, dfdr, dxidr;
     /* r^l with 0^0 = 1 */
     double rl = (l == 0) ? 1.0 : pow(r, (double)l);
-    double f = -rl / pow(1.0 + r, 2.0 * l + 1.0);
+    if (basis == 0) {
+        xi = (r - 1.0) / (r + 1.0);
+        f = -rl / pow(1.0 + r, 2.0 * l + 1.0);
+        /* df/dr = -[l r^(l-1) (1+r)^-(2l+1) - (2l+1) r^l (1+r)^-(2l+2)] */
+        dfdr = (2.0 * l + 1.0) * rl / pow(1.0 + r, 2.0 * l + 2.0);
+        if (l > 0) dfdr -= l * pow(r, l - 1.0) / pow(1.0 + r, 2.0 * l + 1.0);
+        dxidr = 2.0 / ((1.0 + r) * (1.0 + r));
+    } else {
+        double q = 1.0 + r * r;
+        xi = (r * r - 1.0) / q;
+        f = -rl / pow(q, l + 0.5);
+        /* df/dr = -[l r^(l-1) q^-(l+1/2) - (2l+1) r^(l+1) q^-(l+3/2)] */
+        dfdr = (2.0 * l + 1.0) * rl * r / pow(q, l + 1.5);
+        if (l > 0) dfdr -= l * pow(r, l - 1.0) / pow(q, l + 0.5);
+        dxidr = 4.0 * r / (q * q);
+    }
+    double C[64], Cp[64];
+    gegenbauer_all(n_max, alpha, xi, C);
     for (int n = 0; n <= n_max; ++n) phi[n] = f * C[n];
     if (!dphi) return;
     gegenbauer_all(n_max, alpha + 1.0, xi, Cp);
-    /* df/dr = -[l r^(l-1) (1+r)^-(2l+1) - (2l+1) r^l (1+r)^-(2l+2)] */
-    double dfdr = (2.0 * l + 1.0) * rl / pow(1.0 + r, 2.0 * l + 2.0);
-    if (l > 0) dfdr -= l * pow(r, l - 1.0) / pow(1.0 + r, 2.0 * l + 1.0);
-    double dxidr = 2.0 / ((1.0 + r) * (1.0 + r));
     for (int n = 0; n <= n_max; ++n) {
         double dC = (n == 0) ? 0.0 : 2.0 * alpha * Cp[n - 1];
         dphi[n] = dfdr * C[n] + f * dC * dxidr;
     }
 }
 
-int etics_ref_phi_nl(int n, int l, double r, double *phi, double *dphi)
+static void radial_all(int n_max, int l, double r, double *phi, double *dphi)
 {
-    if (n < 0 || l < 0 || n > 60 || r < 0.0 || !phi) return -1;
+    radial_all_b(0, n_max, l, r, phi, dphi);
+}
+
+int etics_ref_phi_nl_b(int basis, int n, int l, double r, double *phi, double *dphi)
+{
+    if ((basis != 0 && basis != 1) || n < 0 || l < 0 || n > 60 || r < 0.0 || !phi) return -1;
     double p[64], dp[64];
-    radial_all(n, l, r, p, dphi ? dp : NULL);
+    radial_all_b(basis, n, l, r, p, dphi ? dp : NULL);
     *phi = p[n];
     if (dphi) *dphi = dp[n];
     return 0;
 }
 
-/* J_nl = int rho_nl phi_nl r^2 dr for the density partner
- *   rho_nl = K_nl/(2 pi) r^(l-1) (1+r)^-(2l+3) C_n^(2l+3/2)(xi),
- *   K_nl   = n (n + 4l + 3)/2 + (l+1)(2l+1),
- * obtained with the Gegenbauer norm
+int etics_ref_phi_nl(int n, int l, double r, double *phi, double *dphi)
+{
+    return etics_ref_phi_nl_b(0, n, l, r, phi, dphi);
+}
+
+/* J_nl = int rho_nl phi_nl r^2 dr for the density partner rho_nl of phi_nl
+ * (laplacian phi_nl Y = 4 pi rho_nl Y), obtained with the Gegenbauer norm
  *   int (1-x^2)^(alpha-1/2) [C_n^alpha]^2 dx
- *       = pi 2^(1-2 alpha) Gamma(n + 2 alpha) / (n! (n + alpha) Gamma(alpha)^2):
- *   J_nl = -K_nl 2^-(8l+6) Gamma(n+4l+3) / (n! (n+2l+3/2) Gamma(2l+3/2)^2).
- * (J_00 = -1/(12 pi).) */
+ *       = pi 2^(1-2 alpha) Gamma(n + 2 alpha) / (n! (n + alpha) Gamma(alpha)^2).
+ * HO92: rho_nl = K_nl/(2 pi) r^(l-1) (1+r)^-(2l+3) C_n^(2l+3/2)(xi),
+ *   K_nl = n (n + 4l + 3)/2 + (l+1)(2l+1),
+ *   J_nl = -K_nl 2^-(8l+6) Gamma(n+4l+3) / (n! (n+2l+3/2) Gamma(2l+3/2)^2)
+ *   (J_00 = -1/(12 pi)).
+ * CB73: rho_nl = K_nl/(4 pi) r^l (1+r^2)^-(l+5/2) C_n^(l+1)(xi),
+ *   K_nl = 4n (n + 2l + 2) + (2l+1)(2l+3),
+ *   J_nl = -K_nl 2^-(4l+6) Gamma(n+2l+2) / (n! (n+l+1) Gamma(l+1)^2)
+ *   (J_00 = -3/64). */
+double etics_ref_jnl_b(int basis, int n, int l)
+{
+    if (basis == 0) {
+        double K = 0.5 * n * (n + 4.0 * l + 3.0) + (l + 1.0) * (2.0 * l + 1.0);
+        double lg = lgamma(n + 4.0 * l + 3.0) - lgamma(n + 1.0)
+                  - 2.0 * lgamma(2.0 * l + 1.5) - (8.0 * l + 6.0) * log(2.0);
+        return -K * exp(lg) / (n + 2.0 * l + 1.5);
+    }
+    double K = 4.0 * n * (n + 2.0 * l + 2.0) + (2.0 * l + 1.0) * (2.0 * l + 3.0);
+    double lg = lgamma(n + 2.0 * l + 2.0) - lgamma(n + 1.0)
+              - 2.0 * lgamma(l + 1.0) - (4.0 * l + 6.0) * log(2.0);
+    return -K * exp(lg) / (n + l + 1.0);
+}
+
 double etics_ref_jnl(int n, int l)
 {
-    double K = 0.5 * n * (n + 4.0 * l + 3.0) + (l + 1.0) * (2.0 * l + 1.0);
-    double lg = lgamma(n + 4.0 * l + 3.0) - lgamma(n + 1.0)
-              - 2.0 * lgamma(2.0 * l + 1.5) - (8.0 * l + 6.0) * log(2.0);
-    return -K * exp(lg) / (n + 2.0 * l + 1.5);
+    return etics_ref_jnl_b(0, n, l);
 }
 
 /* Spherical coordinates of a point.  On the z axis phi = 0; at the origin
@@ -243,11 +289,11 @@ static void parallel_points(point_fn fn, void *ctx, long n, int nthreads)
 /* SCF                                                                       */
 /* ------------------------------------------------------------------------ */
 
-int etics_ref_scf_coeffs(const double *pos, const double *mass, long n_part,
-                         int n_max, int l_max, double *coeffs)
+int etics_ref_scf_coeffs_b(int basis, const double *pos, const double *mass, long n_part,
+                           int n_max, int l_max, double *coeffs)
 {
-    if (n_part < 0 || n_max < 0 || n_max > 60 || l_max < 0 || l_max > 60 ||
-        (n_part > 0 && (!pos || !mass)) || !coeffs)
+    if ((basis != 0 && basis != 1) || n_part < 0 || n_max < 0 || n_max > 60 || l_max < 0 ||
+        l_max > 60 || (n_part > 0 && (!pos || !mass)) || !coeffs)
         return -1;
     int nj = (l_max + 1) * (l_max + 1);
     memset(coeffs, 0, sizeof(double) * (size_t)(n_max + 1) * nj);
@@ -258,7 +304,7 @@ int etics_ref_scf_coeffs(const double *pos, const double *mass, long n_part,
         to_sph(pos[3 * k], pos[3 * k + 1], pos[3 * k + 2], &s);
         ylm_all(l_max, &s, Y, NULL, NULL);
         for (int l = 0; l <= l_max; ++l) {
-            radial_all(n_max, l, s.r, phi, NULL);
+            radial_all_b(basis, n_max, l, s.r, phi, NULL);
             for (int n = 0; n <= n_max; ++n)
                 for (int m = -l; m <= l; ++m) {
                     int j = l * l + l + m;
@@ -268,16 +314,22 @@ int etics_ref_scf_coeffs(const double *pos, const double *mass, long n_part,
     }
     for (int n = 0; n <= n_max; ++n)
         for (int l = 0; l <= l_max; ++l) {
-            double J = etics_ref_jnl(n, l);
+            double J = etics_ref_jnl_b(basis, n, l);
             for (int m = -l; m <= l; ++m) coeffs[(size_t)n * nj + l * l + l + m] /= J;
         }
     free(Y);
     return 0;
 }
 
+int etics_ref_scf_coeffs(const double *pos, const double *mass, long n_part,
+                         int n_max, int l_max, double *coeffs)
+{
+    return etics_ref_scf_coeffs_b(0, pos, mass, n_part, n_max, l_max, coeffs);
+}
+
 typedef struct {
     const double *pos, *coeffs;
-    int n_max, l_max;
+    int n_max, l_max, basis;
     double *acc, *pot;
 } scf_ctx_t;
 
@@ -298,12 +350,13 @@ static void scf_points(void *vctx, long begin, long end)
              * potential.  The gradient of phi_nl Y_lm vanishes there for
              * l = 0 (by symmetry) and l >= 2; for l = 1,
              * phi_n1(r) Y_1m = (phi_n1/r) (r Y_1m) with phi_n1/r -> -C_n(-1). */
-            radial_all(c->n_max, 0, 0.0, phi, NULL);
+            radial_all_b(c->basis, c->n_max, 0, 0.0, phi, NULL);
             double Y00 = 1.0 / sqrt(4.0 * PI);
             for (int n = 0; n <= c->n_max; ++n) P += c->coeffs[(size_t)n * nj] * phi[n] * Y00;
             if (L >= 1) {
+                /* both bases: phi_n1(r) / r -> -C_n^alpha_1(-1) as r -> 0 */
                 double C[64];
-                gegenbauer_all(c->n_max, 3.5, -1.0, C);
+                gegenbauer_all(c->n_max, basis_alpha(c->basis, 1), -1.0, C);
                 for (int n = 0; n <= c->n_max; ++n)
                     for (int m = -1; m <= 1; ++m) {
                         double gv[3];
@@ -316,7 +369,7 @@ static void scf_points(void *vctx, long begin, long end)
             ylm_all(L, &s, Y, Yt, Yp);
             double dr = 0.0, dt = 0.0, dp = 0.0;
             for (int l = 0; l <= L; ++l) {
-                radial_all(c->n_max, l, s.r, phi, dphi);
+                radial_all_b(c->basis, c->n_max, l, s.r, phi, dphi);
                 for (int n = 0; n <= c->n_max; ++n)
                     for (int m = -l; m <= l; ++m) {
                         int j = l * l + l + m;
@@ -336,16 +389,22 @@ static void scf_points(void *vctx, long begin, long end)
     free(Y); free(Yt); free(Yp);
 }
 
+int etics_ref_scf_field_b(int basis, const double *pos, long n_part, int n_max, int l_max,
+                          const double *coeffs, double *acc, double *pot, int nthreads)
+{
+    if ((basis != 0 && basis != 1) || n_part < 0 || n_max < 0 || n_max > 60 || l_max < 0 ||
+        l_max > 60 || (n_part > 0 && !pos) || !coeffs)
+        return -1;
+    scf_ctx_t ctx = {pos, coeffs, n_max, l_max, basis, acc, pot};
+    parallel_points(scf_points, &ctx, n_part, nthreads);
+    return 0;
+}
+
 int etics_ref_scf_field(const double *pos, long n_part, int n_max, int l_max,
                         const double *coeffs, double *acc, double *pot,
                         int nthreads)
 {
-    if (n_part < 0 || n_max < 0 || n_max > 60 || l_max < 0 || l_max > 60 ||
-        (n_part > 0 && !pos) || !coeffs)
-        return -1;
-    scf_ctx_t ctx = {pos, coeffs, n_max, l_max, acc, pot};
-    parallel_points(scf_points, &ctx, n_part, nthreads);
-    return 0;
+    return etics_ref_scf_field_b(0, pos, n_part, n_max, l_max, coeffs, acc, pot, nthreads);
 }
 
 /* ------------------------------------------------------------------------ */

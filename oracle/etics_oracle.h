@@ -62,6 +62,17 @@ int etics_ref_scf_field(const double *pos, long n_part, int n_max, int l_max,
 int etics_ref_mex_field(const double *pos, const double *mass, long n_part,
                         int l_max, double *acc, double *pot, long *order);
 
+/* The same three SCF functions for a chosen radial basis (Sec. 2.5):
+ * basis 0 = Hernquist-Ostriker (as above), basis 1 = Clutton-Brock (the
+ * Plummer model as zeroth term):
+ *   phi_nl = -r^l (1+r^2)^-(l+1/2) C_n^(l+1)(xi),  xi = (r^2-1)/(r^2+1). */
+int etics_ref_phi_nl_b(int basis, int n, int l, double r, double *phi, double *dphi);
+double etics_ref_jnl_b(int basis, int n, int l);
+int etics_ref_scf_coeffs_b(int basis, const double *pos, const double *mass, long n_part,
+                           int n_max, int l_max, double *coeffs);
+int etics_ref_scf_field_b(int basis, const double *pos, long n_part, int n_max, int l_max,
+                          const double *coeffs, double *acc, double *pot, int nthreads);
+
 /* Direct summation (Sec. 2.1 eq. 4), unsoftened, self term excluded. */
 int etics_ref_direct(const double *pos, const double *mass, long n_part,
                      double *acc, double *pot, int nthreads);
