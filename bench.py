@@ -747,7 +747,8 @@ def run_accuracy(args):
     10^3 to 10^6; realisations are stacked up to 10^6 particles per point (at
     most 100).  MEX at l_max = 0, 2, 4, 6; SCF at l_max = 6 with n_max =
     0..14 and at l_max = 10 with n_max = 6, 10, 14 (the paper's Fig. 8 sweep,
-    where SCF approaches MEX as n_max grows).  The overlap of the log10(eps)
+    where SCF approaches MEX as n_max grows), and SCF in the Clutton-Brock
+    basis (Plummer zeroth term) at l_max = 6.  The overlap of the log10(eps)
     histograms of SCF and MEX at l_max = 6 measures that approach."""
     import torch
     from paper_1406_4254_gb300 import etics, inputs, models
@@ -770,7 +771,8 @@ def run_accuracy(args):
 
     methods = ([("mex", 0, l) for l in (0, 2, 4, 6)] +
                [("scf", n, 6) for n in (0, 2, 4, 6, 10, 14)] +
-               [("scf", n, 10) for n in (6, 10, 14)])
+               [("scf", n, 10) for n in (6, 10, 14)] +
+               [("scfcb", n, 6) for n in (0, 2, 6, 10)])
     bins = np.linspace(-9.0, 1.0, 101)
     out = {}
     for model in ("model1", "model2", "hernquist", "plummer"):
@@ -787,7 +789,8 @@ def run_accuracy(args):
                     if kind == "mex":
                         a = etics.mex_field(x, lm)
                     else:
-                        a, _ = etics.scf_force(x, nm, lm)
+                        a, _ = etics.scf_force(x, nm, lm, basis=etics.BASIS_CB
+                                               if kind == "scfcb" else etics.BASIS_HO)
                     a = a.cpu().numpy()[:, :3]
                     errs[meth].append(np.linalg.norm(a - a_real, axis=1) / nr)
             etics.check_error()
@@ -795,13 +798,13 @@ def run_accuracy(args):
             hist = {}
             for meth, es in errs.items():
                 e = np.concatenate(es)
-                key = f"mex_l{meth[2]}" if meth[0] == "mex" else f"scf_n{meth[1]}_l{meth[2]}"
+                key = f"mex_l{meth[2]}" if meth[0] == "mex" else f"{meth[0]}_n{meth[1]}_l{meth[2]}"
                 row[key] = {"mean": float(e.mean()), "median": float(np.median(e)),
                             "p90": float(np.quantile(e, 0.9))}
                 h, _ = np.histogram(np.log10(np.maximum(e, 1e-12)), bins=bins)
                 hist[key] = h / max(1, h.sum())
             row["overlap_with_mex_l6"] = {k: float(np.minimum(hist[k], hist["mex_l6"]).sum())
-                                          for k in hist if k.startswith("scf") and k.endswith("_l6")}
+                                          for k in hist if k.startswith("scf_") and k.endswith("_l6")}
             row["realisations"] = reps
             out[model][str(n)] = row
     return {"experiment": "accuracy", "precision": "FP64",

@@ -91,6 +91,25 @@ int etics_scf_coeffs(const void *posm, int64_t N, int n_max, int l_max, int prec
 int etics_scf_field(const void *posm, int64_t N, int n_max, int l_max, int precision,
                     const double *coeffs, void *accpot, int out_mask, void *stream);
 
+/* The two SCF passes with a chosen radial basis (Sec. 2.5 describes both):
+ *   ETICS_BASIS_HO: Hernquist-Ostriker, the Hernquist model as zeroth term
+ *     (what etics_scf_coeffs / etics_scf_field use);
+ *   ETICS_BASIS_CB: Clutton-Brock, the Plummer model as zeroth term,
+ *     phi_nl = -r^l (1+r^2)^-(l+1/2) C_n^(l+1)(xi), xi = (r^2-1)/(r^2+1),
+ *     J_nl = -K_nl 2^-(4l+6) (n+2l+1)! / (n! (n+l+1) (l!)^2),
+ *     K_nl = 4n(n+2l+2) + (2l+1)(2l+3).
+ * Arguments, layouts, workspace and errors as etics_scf_coeffs /
+ * etics_scf_field; an unknown basis is ETICS_ERR_ARG.  Coefficients of one
+ * basis are meaningless in the other. */
+#define ETICS_BASIS_HO 0
+#define ETICS_BASIS_CB 1
+int etics_scf_coeffs_basis(const void *posm, int64_t N, int n_max, int l_max, int basis,
+                           int precision, double *coeffs, void *ws, size_t ws_bytes,
+                           void *stream);
+int etics_scf_field_basis(const void *posm, int64_t N, int n_max, int l_max, int basis,
+                          int precision, const double *coeffs, void *accpot, int out_mask,
+                          void *stream);
+
 /* MEX force calculation (Sec. 2.4 eqs. 15-17, Sec. 3.2): radial sort, inner
  * and outer exclusive cumulative sums of m r^l Y_lm and m r^-(l+1) Y_lm, and
  * Phi_i = -sum_l 4pi/(2l+1) sum_m [q_lm(i) r^-(l+1) + p_lm(i) r^l] Y_lm(x_i).

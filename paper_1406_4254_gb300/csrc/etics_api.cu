@@ -128,6 +128,54 @@ int etics_scf_field(const void* posm, int64_t N, int n_max, int l_max, int preci
     return rc;
 }
 
+int etics_scf_coeffs_basis(const void* posm, int64_t N, int n_max, int l_max, int basis,
+                           int precision, double* coeffs, void* ws, size_t ws_bytes,
+                           void* stream) {
+    if (basis == ETICS_BASIS_HO)
+        return etics_scf_coeffs(posm, N, n_max, l_max, precision, coeffs, ws, ws_bytes, stream);
+    if (basis != ETICS_BASIS_CB) return ETICS_ERR_ARG;
+    if (!valid_n(N) || !valid_precision(precision) || !coeffs || !aligned(coeffs, 8))
+        return ETICS_ERR_ARG;
+    if (n_max < 0 || l_max < 0) return ETICS_ERR_ARG;
+    if (n_max > ETICS_NMAX_LIMIT || l_max > ETICS_LMAX_LIMIT) return ETICS_ERR_UNSUPPORTED;
+    if (check_particles(posm, N)) return ETICS_ERR_ARG;
+    if (!ws || !aligned(ws, 256)) return ETICS_ERR_ARG;
+    if (ws_bytes < etics_workspace_bytes(N, n_max, l_max, ETICS_SCF, precision))
+        return ETICS_ERR_WORKSPACE;
+    CtxHolder h;
+    int rc = make_ctx(stream, h);
+    if (rc) return rc;
+    etics::stage_event(h.ctx, 0);
+    rc = precision == ETICS_MIXED
+             ? etics::scf_coeffs_cb_f32(posm, N, n_max, l_max, coeffs, ws, h.ctx)
+             : etics::scf_coeffs_cb_f64(posm, N, n_max, l_max, coeffs, ws, h.ctx);
+    etics::stage_event(h.ctx, 2);
+    return rc;
+}
+
+int etics_scf_field_basis(const void* posm, int64_t N, int n_max, int l_max, int basis,
+                          int precision, const double* coeffs, void* accpot, int out_mask,
+                          void* stream) {
+    if (basis == ETICS_BASIS_HO)
+        return etics_scf_field(posm, N, n_max, l_max, precision, coeffs, accpot, out_mask, stream);
+    if (basis != ETICS_BASIS_CB) return ETICS_ERR_ARG;
+    if (!valid_n(N) || !valid_precision(precision) || !coeffs || !aligned(coeffs, 8))
+        return ETICS_ERR_ARG;
+    if (n_max < 0 || l_max < 0) return ETICS_ERR_ARG;
+    if (n_max > ETICS_NMAX_LIMIT || l_max > ETICS_LMAX_LIMIT) return ETICS_ERR_UNSUPPORTED;
+    if ((out_mask & (ETICS_OUT_ACC | ETICS_OUT_POT)) == 0 || (out_mask & ~3)) return ETICS_ERR_ARG;
+    if (check_particles(posm, N) || check_particles(accpot, N)) return ETICS_ERR_ARG;
+    CtxHolder h;
+    int rc = make_ctx(stream, h);
+    if (rc) return rc;
+    etics::stage_event(h.ctx, 0);
+    rc = precision == ETICS_MIXED
+             ? etics::scf_field_cb_f32(posm, N, n_max, l_max, coeffs, accpot, out_mask, h.ctx)
+             : etics::scf_field_cb_f64(posm, N, n_max, l_max, coeffs, accpot, out_mask, h.ctx);
+    etics::stage_event(h.ctx, 1);
+    return rc;
+}
+
 int etics_mex_field(const void* posm, int64_t N, int l_max, int precision, void* accpot,
                     int out_mask, void* ws, size_t ws_bytes, void* stream) {
     if (!valid_n(N) || !valid_precision(precision) || l_max < 0) return ETICS_ERR_ARG;

@@ -93,6 +93,14 @@ struct BasisTables {
     // 1/J_nl, J_nl = -K_nl (n+4l+2)!/n! / (2^(8l+6) (n+2l+3/2) pi prod_{k=0}^{2l}(k+1/2)^2),
     // K_nl = n(n+4l+3)/2 + (l+1)(2l+1)
     double inv_j[kNmaxLimit + 1][kLmaxLimit + 1];
+    // Clutton-Brock basis (Plummer zeroth term): Gegenbauer alpha = l + 1 and
+    // 1/J_nl, J_nl = -K_nl 2^-(4l+6) (n+2l+1)! / (n! (n+l+1) (l!)^2),
+    // K_nl = 4n(n+2l+2) + (2l+1)(2l+3)
+    float ga_cb_f[kLmaxLimit + 1][kNmaxLimit + 1];
+    float gb_cb_f[kLmaxLimit + 1][kNmaxLimit + 1];
+    double ga_cb_d[kLmaxLimit + 1][kNmaxLimit + 1];
+    double gb_cb_d[kLmaxLimit + 1][kNmaxLimit + 1];
+    double inv_j_cb[kNmaxLimit + 1][kLmaxLimit + 1];
 };
 
 constexpr BasisTables make_tables() {
@@ -133,17 +141,77 @@ constexpr BasisTables make_tables() {
             t.inv_j[n][l] = 1.0 / J;
         }
     }
+    for (int l = 0; l <= kLmaxLimit; ++l) {
+        const double alpha = l + 1.0;
+        for (int n = 0; n <= kNmaxLimit; ++n) {
+            double a = 0.0, b = 0.0;
+            if (n >= 1) {
+                a = 2.0 * (n + alpha - 1.0) / n;
+                b = (n + 2.0 * alpha - 2.0) / n;
+            }
+            t.ga_cb_d[l][n] = a;
+            t.gb_cb_d[l][n] = b;
+            t.ga_cb_f[l][n] = (float)a;
+            t.gb_cb_f[l][n] = (float)b;
+            const double K = 4.0 * n * (n + 2.0 * l + 2.0) + (2.0 * l + 1.0) * (2.0 * l + 3.0);
+            double num = 1.0;                         // (n+2l+1)!/n!
+            for (int k = n + 1; k <= n + 2 * l + 1; ++k) num *= (double)k;
+            double den = (n + l + 1.0);
+            for (int k = 2; k <= l; ++k) den *= (double)k * (double)k;   // (l!)^2
+            for (int k = 0; k < 4 * l + 6; ++k) den *= 2.0;
+            t.inv_j_cb[n][l] = 1.0 / (-K * num / den);
+        }
+    }
     return t;
 }
 
 static __constant__ BasisTables c_tab = make_tables();
 
-template <typename R> __device__ __forceinline__ R geg_a(int l, int n);
-template <> __device__ __forceinline__ float geg_a<float>(int l, int n) { return c_tab.ga_f[l][n]; }
-template <> __device__ __forceinline__ double geg_a<double>(int l, int n) { return c_tab.ga_d[l][n]; }
-template <typename R> __device__ __forceinline__ R geg_b(int l, int n);
-template <> __device__ __forceinline__ float geg_b<float>(int l, int n) { return c_tab.gb_f[l][n]; }
-template <> __device__ __forceinline__ double geg_b<double>(int l, int n) { return c_tab.gb_d[l][n]; }
+// Gegenbauer recursion constants of radial basis B (0 Hernquist-Ostriker,
+// 1 Clutton-Brock)
+template <typename R, int B = 0> __device__ __forceinline__ R geg_a(int l, int n) {
+    if constexpr (sizeof(R) == 4) return B == 0 ? c_tab.ga_f[l][n] : c_tab.ga_cb_f[l][n];
+    else return B == 0 ? c_tab.ga_d[l][n] : c_tab.ga_cb_d[l][n];
+}
+template <typename R, int B = 0> __device__ __forceinline__ R geg_b(int l, int n) {
+    if constexpr (sizeof(R) == 4) return B == 0 ? c_tab.gb_f[l][n] : c_tab.gb_cb_f[l][n];
+    else return B == 0 ? c_tab.gb_d[l][n] : c_tab.gb_cb_d[l][n];
+}
+__device__ __forceinline__ double inv_j_of(int basis, int n, int l) {
+    return basis == 0 ? c_tab.inv_j[n][l] : c_tab.inv_j_cb[n][l];
+}
+
+// Radial seeds of basis B at radius r, the form both SCF passes use: the
+// radial factor of level l is phi_nl(r) = pre_l C_n(xi) with
+// pre_l = pre0 st^l = -r^l g(r)^(2l+1), so that phi_nl Y_lm evaluated with
+// the harmonic at the unit vector is pre0 st^l C_n(xi) Z_lm(u):
+//   HO: g = 1/(1+r),       st = r/(1+r)^2, xi = (r-1)/(r+1),     dxi/dr = 2/(1+r)^2
+//   CB: g = 1/sqrt(1+r^2), st = r/(1+r^2), xi = (r^2-1)/(r^2+1), dxi/dr = 4r/(1+r^2)^2
+// with pre0 = -g.  tau enters the radial derivative,
+// d pre_l/dr = pre_l (l/r - (2l+1) tau), tau = 1/(1+r) (HO), r/(1+r^2) (CB);
+// q = st/r = g^2 scales the solid-harmonic gradient term (pre_l / r).
+template <typename R, int B>
+struct RadialSeed {
+    R pre0, st, xi, dxdr, tau, q;
+    __device__ __forceinline__ explicit RadialSeed(R r) {
+        if constexpr (B == 0) {
+            const R t = R(1) / (R(1) + r);
+            pre0 = -t;
+            q = t * t;
+            st = r * q;
+            xi = R(1) - R(2) * t;
+            dxdr = R(2) * q;
+            tau = t;
+        } else {
+            q = R(1) / (R(1) + r * r);
+            pre0 = -sqrt(q);
+            st = r * q;
+            xi = R(1) - R(2) * q;
+            dxdr = R(4) * r * q * q;
+            tau = r * q;
+        }
+    }
+};
 template <typename R> __device__ __forceinline__ R mex_w(int idx);
 template <> __device__ __forceinline__ float mex_w<float>(int idx) { return c_tab.mexw_f[idx]; }
 template <> __device__ __forceinline__ double mex_w<double>(int idx) { return c_tab.mexw_d[idx]; }

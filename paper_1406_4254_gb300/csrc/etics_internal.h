@@ -18,6 +18,16 @@ int scf_field_f32(const void* posm, int64_t N, int n_max, int l_max, const doubl
 int scf_field_f64(const void* posm, int64_t N, int n_max, int l_max, const double* coeffs,
                   void* out, int out_mask, const LaunchCtx& ctx);
 
+// ---- SCF with the Clutton-Brock radial basis (etics_scf_cb_f32/f64.cu) ------
+int scf_coeffs_cb_f32(const void* posm, int64_t N, int n_max, int l_max, double* coeffs, void* ws,
+                      const LaunchCtx& ctx);
+int scf_coeffs_cb_f64(const void* posm, int64_t N, int n_max, int l_max, double* coeffs, void* ws,
+                      const LaunchCtx& ctx);
+int scf_field_cb_f32(const void* posm, int64_t N, int n_max, int l_max, const double* coeffs,
+                     void* out, int out_mask, const LaunchCtx& ctx);
+int scf_field_cb_f64(const void* posm, int64_t N, int n_max, int l_max, const double* coeffs,
+                     void* out, int out_mask, const LaunchCtx& ctx);
+
 // ---- radial sort (etics_sort.cu) -------------------------------------------
 struct SortBuffers {
     uint32_t *keys_a, *keys_b, *vals_a, *vals_b;

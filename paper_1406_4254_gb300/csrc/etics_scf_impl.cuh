@@ -92,11 +92,11 @@ __device__ __forceinline__ void angular_levels(R (&C)[3][LMU + 1], R (&S)[3][LMU
     }
 }
 
-// phase 1, radial part: Rs[l][n][k] = m phi_nl(r_k) = w_l C_n^(2l+3/2)(xi) for
+// phase 1, radial part: Rs[l][n][k] = m phi_nl(r_k) / r^l = w_l C_n(xi) for
 // levels l in [l_begin, l_end] (compile-time recursion over the level, n
 // unrolled to NR so the recursion constants are immediates).  Rows n > n_max
-// stay zero.  w_l = -m (1+r)^-1 (r/(1+r)^2)^l.
-template <typename R, int NR, int L, int LMU>
+// stay zero.  w_l = m pre0 st^l (RadialSeed of basis B).
+template <typename R, int NR, int L, int LMU, int B = 0>
 __device__ __forceinline__ void radial_levels(R* Rs, int T, int k, int n_max, int l_begin,
                                               int l_end, R w, R st, R xi) {
     if constexpr (L <= LMU) {
@@ -108,18 +108,18 @@ __device__ __forceinline__ void radial_levels(R* Rs, int T, int k, int n_max, in
 #pragma unroll
             for (int n = 1; n < NR; ++n) {
                 if (n <= n_max) {
-                    const R cn = geg_a<R>(L, n) * xi * c - geg_b<R>(L, n) * cm1;
+                    const R cn = geg_a<R, B>(L, n) * xi * c - geg_b<R, B>(L, n) * cm1;
                     cm1 = c;
                     c = cn;
                     row[(size_t)n * T] = w * c;
                 }
             }
         }
-        radial_levels<R, NR, L + 1, LMU>(Rs, T, k, n_max, l_begin, l_end, w * st, st, xi);
+        radial_levels<R, NR, L + 1, LMU, B>(Rs, T, k, n_max, l_begin, l_end, w * st, st, xi);
     }
 }
 
-template <typename R, int NR, int LMU>
+template <typename R, int NR, int LMU, int B = 0>
 __global__ void __launch_bounds__(ScfCfg<R>::kThreads, 2)
 scf_coeff_kernel(ScfCoeffParams p) {
     constexpr int TH = ScfCfg<R>::kThreads;
@@ -200,12 +200,11 @@ scf_coeff_kernel(ScfCoeffParams p) {
             if (finite4(cur.x, cur.y, cur.z, cur.w)) { x = cur.x; y = cur.y; z = cur.z; m = cur.w; }
             else if (tid < T) report(p.err, ETICS_ERR_NONFINITE);
             const R r = sqrt(x * x + y * y + z * z);
-            const R t = R(1) / (R(1) + r);
-            const R st = r * t * t;
-            const R xi = R(1) - R(2) * t;
+            const RadialSeed<R, B> rs(r);
             if (tid < T) {
                 // radial levels [0, l_split)
-                radial_levels<R, NR, 0, LMU>(Rs, T, k, p.n_max, 0, p.l_split - 1, -m * t, st, xi);
+                radial_levels<R, NR, 0, LMU, B>(Rs, T, k, p.n_max, 0, p.l_split - 1, m * rs.pre0,
+                                                rs.st, rs.xi);
             } else {
                 // angular basis of every level, then radial levels [l_split, l_max]
                 const R inv = r > R(0) ? R(1) / r : R(0);
@@ -213,8 +212,8 @@ scf_coeff_kernel(ScfCoeffParams p) {
                 const R uu = ux * ux + uy * uy + uz * uz;
                 R C[3][LMU + 1], S[3][LMU + 1];
                 angular_levels<R, 0, LMU>(C, S, ux, uy, uz, uu, p.l_max, Ys, T, k);
-                radial_levels<R, NR, 0, LMU>(Rs, T, k, p.n_max, p.l_split, p.l_max, -m * t, st,
-                                             xi);
+                radial_levels<R, NR, 0, LMU, B>(Rs, T, k, p.n_max, p.l_split, p.l_max,
+                                                m * rs.pre0, rs.st, rs.xi);
             }
         }
         cur = load_particle(tile + gridDim.x);
@@ -256,7 +255,7 @@ scf_coeff_kernel(ScfCoeffParams p) {
 // Sum the per-block partials in a fixed order and apply K_lm / J_nl.
 // One warp per output coefficient c[n][l*l+l+m].
 static __global__ void scf_finalize_kernel(const double* __restrict__ partial, int nblocks, int n_max,
-                                    int l_max, int NR, double* __restrict__ coeffs) {
+                                    int l_max, int NR, int basis, double* __restrict__ coeffs) {
     const int nj = (l_max + 1) * (l_max + 1);
     const int nc = (n_max + 1) * nj;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -276,7 +275,7 @@ static __global__ void scf_finalize_kernel(const double* __restrict__ partial, i
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) {
         const int am = m < 0 ? -m : m;
-        coeffs[warp] = s * c_tab.knorm[l * (l + 1) / 2 + am] * c_tab.inv_j[n][l];
+        coeffs[warp] = s * c_tab.knorm[l * (l + 1) / 2 + am] * inv_j_of(basis, n, l);
     }
 }
 
@@ -286,10 +285,11 @@ static __global__ void scf_finalize_kernel(const double* __restrict__ partial, i
 // NM1 > 0: specialised for n_max + 1 == NM1 and l_max == LM (n loop unrolled,
 // coefficient row stride and recursion constants known at compile time);
 // NM1 == 0: generic, n_max and l_max <= LM at run time.
-template <typename R, int LM, bool ACC, int NM1>
+template <typename R, int LM, bool ACC, int NM1, int BASIS = 0>
 struct FieldEval {
     using V4 = Vec4<R>;
     R C[3][LM + 1], S[3][LM + 1];
+    // t: the basis's tau (radial derivative factor), see RadialSeed
     R ux, uy, uz, uu, t, xi, dxdr, st, pre, preR;
     R pot, gr, gx, gy, gz;
     const R* cs;
@@ -315,7 +315,7 @@ struct FieldEval {
 #pragma unroll (NM1 > 0 ? NM1 : 1)
             for (int n = 0; n <= nlim; ++n, row += stride) {
                 if (n > 0) {
-                    const R a = geg_a<R>(L, n), b = geg_b<R>(L, n);
+                    const R a = geg_a<R, BASIS>(L, n), b = geg_b<R, BASIS>(L, n);
                     const R cnew = a * xi * cn - b * cm1;
                     if (ACC) {
                         const R dnew = a * (cn + xi * dn) - b * dm1;
@@ -383,7 +383,7 @@ struct FieldEval {
     }
 };
 
-template <typename R, int LM, bool ACC, int NM1>
+template <typename R, int LM, bool ACC, int NM1, int B = 0>
 __global__ void __launch_bounds__(kFieldThreads, 2)
 scf_field_kernel(const Vec4<R>* __restrict__ posm, int64_t N, int n_max, int l_max,
                  const double* __restrict__ coeffs, Vec4<R>* __restrict__ out, int out_mask,
@@ -409,17 +409,18 @@ scf_field_kernel(const Vec4<R>* __restrict__ posm, int64_t N, int n_max, int l_m
          i += (int64_t)gridDim.x * blockDim.x) {
         const Vec4<R> pv = ld4(posm + i);
         if (!finite4(pv.x, pv.y, pv.z, pv.w)) report(err, ETICS_ERR_NONFINITE);
-        FieldEval<R, LM, ACC, NM1> f;
+        FieldEval<R, LM, ACC, NM1, B> f;
         const R r = sqrt(pv.x * pv.x + pv.y * pv.y + pv.z * pv.z);
         const R inv = r > R(0) ? R(1) / r : R(0);
         f.ux = pv.x * inv; f.uy = pv.y * inv; f.uz = pv.z * inv;
         f.uu = f.ux * f.ux + f.uy * f.uy + f.uz * f.uz;
-        f.t = R(1) / (R(1) + r);
-        f.st = r * f.t * f.t;
-        f.xi = R(1) - R(2) * f.t;
-        f.dxdr = R(2) * f.t * f.t;
-        f.pre = -f.t;
-        f.preR = -f.t * f.t * f.t;
+        const RadialSeed<R, B> rs(r);
+        f.t = rs.tau;
+        f.st = rs.st;
+        f.xi = rs.xi;
+        f.dxdr = rs.dxdr;
+        f.pre = rs.pre0;
+        f.preR = rs.pre0 * rs.q;
         f.pot = f.gr = f.gx = f.gy = f.gz = R(0);
         f.cs = cs;
         f.ncols = ncols;
@@ -480,16 +481,16 @@ inline size_t scf_workspace(int64_t N, int n_max, int l_max, int num_sms) {
     return (size_t)2 * num_sms * W * NR * 4 * sizeof(double);
 }
 
-template <typename R, int NR>
+template <typename R, int NR, int B = 0>
 inline int launch_coeff_nr(const ScfCoeffParams& p, int lmu, int grid, size_t smem,
                            cudaStream_t s) {
     if (lmu <= 6) {
-        auto k = scf_coeff_kernel<R, NR, 6>;
+        auto k = scf_coeff_kernel<R, NR, 6, B>;
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
             return ETICS_ERR_CUDA;
         k<<<grid, ScfCfg<R>::kThreads, smem, s>>>(p);
     } else {
-        auto k = scf_coeff_kernel<R, NR, kLmaxLimit>;
+        auto k = scf_coeff_kernel<R, NR, kLmaxLimit, B>;
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
             return ETICS_ERR_CUDA;
         k<<<grid, ScfCfg<R>::kThreads, smem, s>>>(p);
@@ -497,7 +498,7 @@ inline int launch_coeff_nr(const ScfCoeffParams& p, int lmu, int grid, size_t sm
     return cudaGetLastError() == cudaSuccess ? ETICS_OK : ETICS_ERR_CUDA;
 }
 
-template <typename R>
+template <typename R, int B = 0>
 inline int scf_coeffs_launch(const void* posm, int64_t N, int n_max, int l_max, double* coeffs,
                              void* ws, const LaunchCtx& ctx) {
     int NR, T, W, G, ntiles, grid;
@@ -531,11 +532,11 @@ inline int scf_coeffs_launch(const void* posm, int64_t N, int n_max, int l_max, 
     if (ntiles > 0) {
         int rc;
         switch (NR) {
-            case 4: rc = launch_coeff_nr<R, 4>(p, l_max, grid, smem, ctx.stream); break;
-            case 8: rc = launch_coeff_nr<R, 8>(p, l_max, grid, smem, ctx.stream); break;
-            case 11: rc = launch_coeff_nr<R, 11>(p, l_max, grid, smem, ctx.stream); break;
-            case 15: rc = launch_coeff_nr<R, 15>(p, l_max, grid, smem, ctx.stream); break;
-            default: rc = launch_coeff_nr<R, 17>(p, l_max, grid, smem, ctx.stream); break;
+            case 4: rc = launch_coeff_nr<R, 4, B>(p, l_max, grid, smem, ctx.stream); break;
+            case 8: rc = launch_coeff_nr<R, 8, B>(p, l_max, grid, smem, ctx.stream); break;
+            case 11: rc = launch_coeff_nr<R, 11, B>(p, l_max, grid, smem, ctx.stream); break;
+            case 15: rc = launch_coeff_nr<R, 15, B>(p, l_max, grid, smem, ctx.stream); break;
+            default: rc = launch_coeff_nr<R, 17, B>(p, l_max, grid, smem, ctx.stream); break;
         }
         if (rc) return rc;
         ++*ctx.launches;
@@ -546,13 +547,13 @@ inline int scf_coeffs_launch(const void* posm, int64_t N, int n_max, int l_max, 
     const int threads = 256;
     const int blocks = (nc * 32 + threads - 1) / threads;
     scf_finalize_kernel<<<blocks, threads, 0, ctx.stream>>>(p.partial, nblocks, n_max, l_max, NR,
-                                                            coeffs);
+                                                            B, coeffs);
     if (cudaGetLastError() != cudaSuccess) return ETICS_ERR_CUDA;
     ++*ctx.launches;
     return ETICS_OK;
 }
 
-template <typename R, int LM, int NM1 = 0>
+template <typename R, int LM, int NM1 = 0, int B = 0>
 inline int launch_field_lm(const void* posm, int64_t N, int n_max, int l_max,
                            const double* coeffs, void* out, int out_mask, const LaunchCtx& ctx) {
     const size_t smem = (size_t)(n_max + 1) * col_total(l_max) * sizeof(R);
@@ -563,14 +564,14 @@ inline int launch_field_lm(const void* posm, int64_t N, int n_max, int l_max,
     const Vec4<R>* pp = reinterpret_cast<const Vec4<R>*>(posm);
     Vec4<R>* op = reinterpret_cast<Vec4<R>*>(out);
     if (out_mask & ETICS_OUT_ACC) {
-        auto k = scf_field_kernel<R, LM, true, NM1>;
+        auto k = scf_field_kernel<R, LM, true, NM1, B>;
         if (smem > 48 * 1024 &&
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
             return ETICS_ERR_CUDA;
         k<<<grid, kFieldThreads, smem, ctx.stream>>>(pp, N, n_max, l_max, coeffs, op, out_mask,
                                                      ctx.err);
     } else {
-        auto k = scf_field_kernel<R, LM, false, NM1>;
+        auto k = scf_field_kernel<R, LM, false, NM1, B>;
         if (smem > 48 * 1024 &&
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
             return ETICS_ERR_CUDA;
@@ -580,6 +581,25 @@ inline int launch_field_lm(const void* posm, int64_t N, int n_max, int l_max,
     if (cudaGetLastError() != cudaSuccess) return ETICS_ERR_CUDA;
     ++*ctx.launches;
     return ETICS_OK;
+}
+
+// the generic field kernels for radial basis B
+template <typename R, int B>
+inline int scf_field_launch_generic(const void* posm, int64_t N, int n_max, int l_max,
+                                    const double* coeffs, void* out, int out_mask,
+                                    const LaunchCtx& ctx) {
+    if (N == 0) return ETICS_OK;
+    if (l_max <= 2)
+        return launch_field_lm<R, 2, 0, B>(posm, N, n_max, l_max, coeffs, out, out_mask, ctx);
+    if (l_max <= 4)
+        return launch_field_lm<R, 4, 0, B>(posm, N, n_max, l_max, coeffs, out, out_mask, ctx);
+    if (l_max <= 6)
+        return launch_field_lm<R, 6, 0, B>(posm, N, n_max, l_max, coeffs, out, out_mask, ctx);
+    if (l_max <= 8)
+        return launch_field_lm<R, 8, 0, B>(posm, N, n_max, l_max, coeffs, out, out_mask, ctx);
+    if (l_max <= 10)
+        return launch_field_lm<R, 10, 0, B>(posm, N, n_max, l_max, coeffs, out, out_mask, ctx);
+    return launch_field_lm<R, 14, 0, B>(posm, N, n_max, l_max, coeffs, out, out_mask, ctx);
 }
 
 template <typename R>

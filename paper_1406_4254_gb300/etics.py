@@ -80,6 +80,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.etics_scf_batch.argtypes = [vp, vp, vp, i32, vp, vp, i32, vp, sz, vp]
         lib.etics_leapfrog_step.argtypes = [vp, vp, vp, i64, dbl, i32, i32, i32, i32, vp, vp, sz,
                                             vp]
+        lib.etics_scf_coeffs_basis.argtypes = [vp, i64, i32, i32, i32, i32, vp, vp, sz, vp]
+        lib.etics_scf_field_basis.argtypes = [vp, i64, i32, i32, i32, i32, vp, vp, i32, vp]
         lib.etics_leapfrog_step_coeffs.argtypes = [vp, vp, vp, i64, dbl, i32, i32, i32, vp, vp]
         mp = ctypes.POINTER(MlpShape)
         lib.etics_mlp_param_count.argtypes = [mp]
@@ -103,7 +105,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         for name in ("etics_scf_coeffs", "etics_scf_field", "etics_mex_field",
                      "etics_radial_sort", "etics_radial_keys", "etics_leapfrog_step",
                      "etics_scf_coeffs_noalloc", "etics_scf_batch_plan", "etics_scf_batch",
-                     "etics_leapfrog_step_coeffs", "etics_mlp_forward", "etics_mlp_loss_grad",
+                     "etics_leapfrog_step_coeffs", "etics_mlp_forward",
+                     "etics_scf_coeffs_basis", "etics_scf_field_basis", "etics_mlp_loss_grad",
                      "etics_mlp_adam", "etics_mlp_to_bf16", "etics_coeff_stats",
                      "etics_coeff_features", "etics_coeff_advance", "etics_force_error",
                      "etics_get_error",
@@ -166,9 +169,13 @@ def _aligned_ptr(buf: torch.Tensor) -> tuple[int, int]:
     return q, buf.numel() - (q - p)
 
 
+BASIS_HO, BASIS_CB = 0, 1
+
+
 def scf_coeffs(posm: torch.Tensor, n_max: int, l_max: int, out: torch.Tensor | None = None,
-               ws: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """SCF coefficients c[n, l*l+l+m] (float64, shape (n_max+1, (l_max+1)^2))."""
+               ws: torch.Tensor | None = None, stream=None, basis: int = BASIS_HO) -> torch.Tensor:
+    """SCF coefficients c[n, l*l+l+m] (float64, shape (n_max+1, (l_max+1)^2));
+    basis BASIS_HO (Hernquist-Ostriker, default) or BASIS_CB (Clutton-Brock)."""
     posm = _particles(posm, "posm")
     prec = _precision(posm)
     n = posm.shape[0]
@@ -177,8 +184,13 @@ def scf_coeffs(posm: torch.Tensor, n_max: int, l_max: int, out: torch.Tensor | N
     if ws is None:
         ws = workspace(n, n_max, l_max, SCF, prec, posm.device)
     wp, wb = _aligned_ptr(ws)
-    _check(load().etics_scf_coeffs(posm.data_ptr(), n, n_max, l_max, prec, out.data_ptr(), wp, wb,
-                                   _stream(stream)), "etics_scf_coeffs")
+    if basis == BASIS_HO:
+        rc = load().etics_scf_coeffs(posm.data_ptr(), n, n_max, l_max, prec, out.data_ptr(), wp,
+                                     wb, _stream(stream))
+    else:
+        rc = load().etics_scf_coeffs_basis(posm.data_ptr(), n, n_max, l_max, int(basis), prec,
+                                           out.data_ptr(), wp, wb, _stream(stream))
+    _check(rc, "etics_scf_coeffs")
     return out
 
 
@@ -198,7 +210,7 @@ def scf_coeffs_noalloc(posm: torch.Tensor, n_max: int, l_max: int,
 
 def scf_field(posm: torch.Tensor, coeffs: torch.Tensor, n_max: int, l_max: int,
               out: torch.Tensor | None = None, out_mask: int = OUT_ACC | OUT_POT,
-              stream=None) -> torch.Tensor:
+              stream=None, basis: int = BASIS_HO) -> torch.Tensor:
     """SCF (ax, ay, az, Phi) at each particle of posm."""
     posm = _particles(posm, "posm")
     prec = _precision(posm)
@@ -208,16 +220,22 @@ def scf_field(posm: torch.Tensor, coeffs: torch.Tensor, n_max: int, l_max: int,
         raise ValueError("coefficient count does not match (n_max, l_max)")
     if out is None:
         out = torch.empty_like(posm)
-    _check(load().etics_scf_field(posm.data_ptr(), posm.shape[0], n_max, l_max, prec,
-                                  coeffs.data_ptr(), out.data_ptr(), out_mask, _stream(stream)),
-           "etics_scf_field")
+    if basis == BASIS_HO:
+        rc = load().etics_scf_field(posm.data_ptr(), posm.shape[0], n_max, l_max, prec,
+                                    coeffs.data_ptr(), out.data_ptr(), out_mask, _stream(stream))
+    else:
+        rc = load().etics_scf_field_basis(posm.data_ptr(), posm.shape[0], n_max, l_max,
+                                          int(basis), prec, coeffs.data_ptr(), out.data_ptr(),
+                                          out_mask, _stream(stream))
+    _check(rc, "etics_scf_field")
     return out
 
 
-def scf_force(posm: torch.Tensor, n_max: int, l_max: int, out=None, stream=None):
+def scf_force(posm: torch.Tensor, n_max: int, l_max: int, out=None, stream=None,
+              basis: int = BASIS_HO):
     """Both SCF passes; returns (accpot, coeffs)."""
-    c = scf_coeffs(posm, n_max, l_max, stream=stream)
-    return scf_field(posm, c, n_max, l_max, out=out, stream=stream), c
+    c = scf_coeffs(posm, n_max, l_max, stream=stream, basis=basis)
+    return scf_field(posm, c, n_max, l_max, out=out, stream=stream, basis=basis), c
 
 
 def mex_field(posm: torch.Tensor, l_max: int, out: torch.Tensor | None = None,
