@@ -815,6 +815,48 @@ def run_accuracy(args):
             "results": out}
 
 
+def run_gemm(args):
+    """The MLP's bf16 product on the tcgen05 kernel at a size that fills the
+    GPU: one layer K -> N over M rows (M = 16384, N = K = 4096 by default),
+    y = x W + b.  The product kernel's time comes from the library's stage
+    events around it; achieved = 2 M N K / that time, against the measured
+    cuBLAS bf16 peak."""
+    import torch
+    from paper_1406_4254_gb300 import etics, surrogate
+    dev = torch.device("cuda", 0)
+    M, N, K = args.gemm_mnk
+    net = surrogate.Mlp([K, N], seed=args.seed, device=dev)
+    g = torch.Generator(device=dev).manual_seed(args.seed)
+    x = torch.randn((M, K), generator=g, device=dev).to(torch.bfloat16)
+    y = torch.empty((M, N), dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        net.forward(x, y)
+    torch.cuda.synchronize()
+    rev = RawEvents(3)
+    gemm_ms, epi_ms = [], []
+    for _ in range(args.steps):
+        etics.set_stage_events(rev.handles(0, 3))
+        net.forward(x, y)
+        etics.set_stage_events(None)
+        torch.cuda.synchronize()
+        gemm_ms.append(rev.ms(0, 1))
+        epi_ms.append(rev.ms(1, 2))
+    etics.check_error()
+    peaks, src = load_peaks()
+    ms = statistics.median(gemm_ms)
+    tf = 2.0 * M * N * K / (ms * 1e-3) / 1e12
+    # spot check against a float32 product of the same bf16 operands
+    w = net.params_bf16[:K * N].view(K, N).float()
+    idx = torch.randint(0, M, (64,), generator=g, device=dev)
+    ref = x[idx].float() @ w + net.params[K * N:].view(1, N)
+    err = float(((y[idx] - ref).abs().max() / ref.abs().max()).item())
+    return {"experiment": "gemm", "kernel": "tc::gemm_kernel (tcgen05.mma kind::f16, TMEM accumulator)",
+            "M": M, "N": N, "K": K, "product_ms": ms, "epilogue_ms": statistics.median(epi_ms),
+            "achieved_tflops": tf, "peak_tflops": peaks["bf16_tflops"],
+            "frac": tf / peaks["bf16_tflops"], "peak_source": f"bf16_tflops of MEASURED_PEAKS.json ({src})",
+            "max_rel_err_vs_fp32_product": err}
+
+
 def emit(obj):
     print(json.dumps(obj), flush=True)
 
@@ -830,8 +872,9 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=65536)
-    ap.add_argument("--experiment", choices=["leapfrog", "batch", "surrogate", "accuracy"],
+    ap.add_argument("--experiment", choices=["leapfrog", "batch", "surrogate", "accuracy", "gemm"],
                     default=None)
+    ap.add_argument("--gemm-mnk", type=int, nargs=3, default=[16384, 4096, 4096])
     ap.add_argument("--acc-n", type=int, nargs="+", default=[1000, 10000, 100000, 1000000])
     ap.add_argument("--lf-steps", type=int, default=100)
     ap.add_argument("--sur-n", type=int, default=1 << 26)
@@ -844,6 +887,9 @@ def main():
         return
     if args.experiment == "accuracy":
         emit(run_accuracy(args))
+        return
+    if args.experiment == "gemm":
+        emit(run_gemm(args))
         return
     if args.experiment == "leapfrog":
         emit(run_leapfrog(args))

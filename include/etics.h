@@ -299,7 +299,9 @@ uint64_t etics_launch_count(void);
  * events[k] (cudaEvent_t) at stage boundaries on their stream:
  *   SCF coeffs: 0 start, 1 after the coefficient kernel, 2 end;
  *   SCF field : 0 start, 1 end;
- *   MEX       : 0 start, 1 keys, 2 sorted, 3 tile sums, 4 carries, 5 end.
+ *   MEX       : 0 start, 1 keys, 2 sorted, 3 tile sums, 4 carries, 5 end;
+ *   MLP       : per product 0 start, 1 after the product, 2 after its epilogue
+ *               (a multi-layer call keeps the last product's events).
  * n_events is the array length (recording stops at it).  NULL disables.
  * Not thread-safe: for single-threaded benchmarking. */
 int etics_set_stage_events(void **events, int n_events);

@@ -513,6 +513,7 @@ int gemm(const bf16* A, int64_t lda, const bf16* Bm, int64_t ldb, int M, int N, 
          const float* bias, int act, const float* h, float* out, bf16* out_b,
          const LaunchCtx& ctx) {
     const GemmShape s = gemm_shape(M, N, K);
+    stage_event(ctx, 0);
     if (s.tc) {
         auto k = tc::gemm_kernel<TA, TB>;
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -527,9 +528,11 @@ int gemm(const bf16* A, int64_t lda, const bf16* Bm, int64_t ldb, int M, int N, 
                                                                       N, K, s.kslice);
     }
     if (cudaGetLastError()) return ETICS_ERR_CUDA;
+    stage_event(ctx, 1);
     mlp_epilogue_kernel<<<grid_1d((int64_t)M * N, ctx), 256, 0, ctx.stream>>>(
         part, s.splits, M, N, bias, act, h, out, out_b);
     if (cudaGetLastError()) return ETICS_ERR_CUDA;
+    stage_event(ctx, 2);
     *ctx.launches += 2;
     return ETICS_OK;
 }

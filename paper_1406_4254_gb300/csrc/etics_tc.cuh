@@ -165,19 +165,17 @@ __device__ __forceinline__ void stage(bf16* T, const bf16* __restrict__ X, int64
                 for (int e = 0; e < 8; ++e) dst[e] = (gr < R && gk + e < ke) ? src[e] : zero;
             }
         } else {
-            const int k = chunk >> 4, rc = (chunk & 15) * 8;
-            const int gk = k0 + k, gr = r0 + rc;
+            // r contiguous in memory: each thread gathers 8 consecutive k of one
+            // row (8 two-byte loads, each coalesced across the warp's
+            // consecutive rows) and writes them as one 16-byte core-matrix row
+            const int r = chunk & (kM - 1), kc = (chunk >> 7) * 8;
+            const int gr = r0 + r, gk = k0 + kc;
             const bf16* src = X + (int64_t)gk * ld + gr;
-            if (gk < ke && gr + 8 <= R && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
-                const uint4 v = *reinterpret_cast<const uint4*>(src);
-                const bf16* e8 = reinterpret_cast<const bf16*>(&v);
+            alignas(16) bf16 v[8];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) T[tile_offset(rc + e, k)] = e8[e];
-            } else {
-#pragma unroll
-                for (int e = 0; e < 8; ++e)
-                    T[tile_offset(rc + e, k)] = (gk < ke && gr + e < R) ? src[e] : zero;
-            }
+            for (int e = 0; e < 8; ++e)
+                v[e] = (gr < R && gk + e < ke) ? src[(int64_t)e * ld] : zero;
+            *reinterpret_cast<uint4*>(T + tile_offset(r, kc)) = *reinterpret_cast<const uint4*>(v);
         }
     }
 }
