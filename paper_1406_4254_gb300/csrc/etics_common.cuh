@@ -275,6 +275,52 @@ __device__ __forceinline__ void harm_grad(const R* C1, const R* S1, int m, R gc[
     }
 }
 
+// v += grad sum_m (ac[m] C_L^m + as[m] S_L^m) (as[0] unused), from the level
+// L-1 values.  The ladder relations above, regrouped by the level L-1
+// harmonic they multiply: each direction becomes one dot product with lowered
+// coefficients, 2L-1 terms instead of 2L+1 gradient triples.
+template <typename R, int L>
+__device__ __forceinline__ void grad_contract(const R* C1, const R* S1, const R* ac, const R* as,
+                                              R& vx, R& vy, R& vz) {
+    if constexpr (L >= 1) {
+#pragma unroll
+        for (int k = 0; k <= L - 1; ++k) {
+            // coefficients of C_{L-1}^k
+            R xc = R(0), yc = R(0);
+            if (k + 1 <= L) {
+                const R h = R(0.5 * (L + k + 1) * (L + k));
+                xc = h * ac[k + 1];
+                yc = (k + 1 >= 1) ? h * as[k + 1] : R(0);
+            }
+            if (k >= 2) {
+                xc = fma(R(-0.5), ac[k - 1], xc);
+                yc = fma(R(0.5), as[k - 1], yc);
+            }
+            if (k == 1) xc -= ac[0];
+            vx = fma(xc, C1[k], vx);
+            vy = fma(yc, C1[k], vy);
+            vz = fma(R(L + k) * ac[k], C1[k], vz);
+            if (k >= 1) {
+                // coefficients of S_{L-1}^k
+                R xs = R(0), ys = R(0);
+                if (k + 1 <= L) {
+                    const R h = R(0.5 * (L + k + 1) * (L + k));
+                    xs = h * as[k + 1];
+                    ys = -h * ac[k + 1];
+                }
+                if (k >= 2) {
+                    xs = fma(R(-0.5), as[k - 1], xs);
+                    ys = fma(R(-0.5), ac[k - 1], ys);
+                }
+                if (k == 1) ys -= ac[0];
+                vx = fma(xs, S1[k], vx);
+                vy = fma(ys, S1[k], vy);
+                vz = fma(R(L + k) * as[k], S1[k], vz);
+            }
+        }
+    }
+}
+
 // column layout of one harmonic level: col 0 = C_l^0, col 2m-1 = C_l^m,
 // col 2m = S_l^m (m >= 1); 2l+1 columns, padded to a multiple of 4.
 __host__ __device__ __forceinline__ int ncol_pad(int l) { return ((2 * l + 1 + 3) / 4) * 4; }

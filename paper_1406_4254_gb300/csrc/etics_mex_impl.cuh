@@ -128,24 +128,20 @@ __device__ __forceinline__ void mex_fwd(R (&C)[3][kMexLB + 1], R (&S)[3][kMexLB 
         harm_level<R, L>(C[s1], S[s1], C[s2], S[s2], pt.ux, pt.uy, pt.uz, pt.uu, C[s0], S[s0]);
         if (!pt.origin) {
             R P = R(0), vx = R(0), vy = R(0), vz = R(0);
+            R qc[L + 1], qs[L + 1];
 #pragma unroll
             for (int mm = 0; mm <= L; ++mm) {
                 const R w = mex_w<R>(L * (L + 1) / 2 + mm);
                 const int cc = L * L + (mm == 0 ? 0 : 2 * mm - 1);
-                const R qc = w * q[cc];
-                P = fma(qc, C[s0][mm], P);
-                R qs = R(0);
+                qc[mm] = w * q[cc];
+                P = fma(qc[mm], C[s0][mm], P);
+                qs[mm] = R(0);
                 if (mm > 0) {
-                    qs = w * q[cc + 1];
-                    P = fma(qs, S[s0][mm], P);
-                }
-                if (ACC && L >= 1) {
-                    R gc[3], gs[3];
-                    harm_grad<R, L>(C[s1], S[s1], mm, gc, gs);
-                    vx = fma(qc, gc[0], vx); vy = fma(qc, gc[1], vy); vz = fma(qc, gc[2], vz);
-                    if (mm > 0) { vx = fma(qs, gs[0], vx); vy = fma(qs, gs[1], vy); vz = fma(qs, gs[2], vz); }
+                    qs[mm] = w * q[cc + 1];
+                    P = fma(qs[mm], S[s0][mm], P);
                 }
             }
+            if (ACC && L >= 1) grad_contract<R, L>(C[s1], S[s1], qc, qs, vx, vy, vz);
             pot = fma(rinv, P, pot);
             if (ACC) {
                 const R f = rinv * irho;
@@ -175,24 +171,20 @@ __device__ __forceinline__ void mex_rev(R (&C)[3][kMexLB + 1], R (&S)[3][kMexLB 
         constexpr int s0 = L % 3, s1 = (L + 2) % 3, s2 = (L + 1) % 3;
         harm_level<R, L>(C[s1], S[s1], C[s2], S[s2], pt.ux, pt.uy, pt.uz, pt.uu, C[s0], S[s0]);
         R P = R(0), vx = R(0), vy = R(0), vz = R(0);
+        R pc[L + 1], ps[L + 1];
 #pragma unroll
         for (int mm = 0; mm <= L; ++mm) {
             const R w = mex_w<R>(L * (L + 1) / 2 + mm);
             const int cc = L * L + (mm == 0 ? 0 : 2 * mm - 1);
-            const R pc = w * p[cc];
-            P = fma(pc, C[s0][mm], P);
-            R ps = R(0);
+            pc[mm] = w * p[cc];
+            P = fma(pc[mm], C[s0][mm], P);
+            ps[mm] = R(0);
             if (mm > 0) {
-                ps = w * p[cc + 1];
-                P = fma(ps, S[s0][mm], P);
-            }
-            if (ACC && L >= 1) {
-                R gc[3], gs[3];
-                harm_grad<R, L>(C[s1], S[s1], mm, gc, gs);
-                vx = fma(pc, gc[0], vx); vy = fma(pc, gc[1], vy); vz = fma(pc, gc[2], vz);
-                if (mm > 0) { vx = fma(ps, gs[0], vx); vy = fma(ps, gs[1], vy); vz = fma(ps, gs[2], vz); }
+                ps[mm] = w * p[cc + 1];
+                P = fma(ps[mm], S[s0][mm], P);
             }
         }
+        if (ACC && L >= 1) grad_contract<R, L>(C[s1], S[s1], pc, ps, vx, vy, vz);
         pot = fma(rl, P, pot);
         if (ACC && L >= 1) {
             ax = fma(rlm1, vx, ax);

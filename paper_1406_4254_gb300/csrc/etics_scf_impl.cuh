@@ -356,21 +356,13 @@ struct FieldEval {
                 gr = fma(pre, R(-(2 * L + 1)) * t * P + dxdr * Q, gr);
                 if constexpr (L >= 1) {
                     R vx = R(0), vy = R(0), vz = R(0);
+                    R ac[L + 1], as[L + 1];
 #pragma unroll
                     for (int m = 0; m <= L; ++m) {
-                        R gc[3], gs[3];
-                        harm_grad<R, L>(C[s1], S[s1], m, gc, gs);
-                        const R ac = A[m == 0 ? 0 : 2 * m - 1];
-                        vx = fma(ac, gc[0], vx);
-                        vy = fma(ac, gc[1], vy);
-                        vz = fma(ac, gc[2], vz);
-                        if (m > 0) {
-                            const R as = A[2 * m];
-                            vx = fma(as, gs[0], vx);
-                            vy = fma(as, gs[1], vy);
-                            vz = fma(as, gs[2], vz);
-                        }
+                        ac[m] = A[m == 0 ? 0 : 2 * m - 1];
+                        as[m] = m == 0 ? R(0) : A[2 * m];
                     }
+                    grad_contract<R, L>(C[s1], S[s1], ac, as, vx, vy, vz);
                     gx = fma(preR, vx, gx);
                     gy = fma(preR, vy, gy);
                     gz = fma(preR, vz, gz);
