@@ -168,11 +168,15 @@ scf_coeff_bins_kernel(ScfBinParams p) {
     constexpr int NCOL = (LM + 1) * (LM + 1);
     constexpr int NOUT = NB * NR * kBinCap;
     using V4 = Vec4<R>;
-    // dynamic shared memory: accd [NOUT] doubles, s_rad [T], Ys [NCOL][T]
+    // dynamic shared memory: accd [NOUT] doubles, then two buffers of
+    // s_rad [T] and Ys [NCOL][T]: the basis of the next tile is evaluated into
+    // one while the warps contract the current tile from the other
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* accd = reinterpret_cast<double*>(smem_raw);
-    V4* s_rad = reinterpret_cast<V4*>(smem_raw + ((NOUT * sizeof(double) + 15) / 16) * 16);
-    R* Ys = reinterpret_cast<R*>(s_rad + T);
+    V4* s_rad0 = reinterpret_cast<V4*>(smem_raw + ((NOUT * sizeof(double) + 15) / 16) * 16);
+    R* Ys0 = reinterpret_cast<R*>(s_rad0 + T);
+    V4* s_rad1 = reinterpret_cast<V4*>(Ys0 + (size_t)NCOL * T);
+    R* Ys1 = reinterpret_cast<R*>(s_rad1 + T);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const V4* posm = reinterpret_cast<const V4*>(p.posm);
     for (int e = tid; e < NOUT; e += T) accd[e] = 0.0;
@@ -195,36 +199,40 @@ scf_coeff_bins_kernel(ScfBinParams p) {
                 acc[n][c] = R(0);
             }
     };
+    auto load = [&](int tile) -> V4 {
+        const int64_t gi = (int64_t)tile * T + tid;
+        return (tile < p.ntiles && gi < p.N) ? ld4(posm + gi) : mk4<R>(R(0), R(0), R(0), R(0));
+    };
+    // phase 1: one particle per thread -> angular basis + radial seeds
+    auto basis = [&](const V4& cur, V4* s_rad, R* Ys) {
+        R x = R(0), y = R(0), z = R(0), m = R(0);
+        if (finite4(cur.x, cur.y, cur.z, cur.w)) { x = cur.x; y = cur.y; z = cur.z; m = cur.w; }
+        else report(p.err, ETICS_ERR_NONFINITE);
+        const R r = sqrt(x * x + y * y + z * z);
+        const R t = R(1) / (R(1) + r);
+        s_rad[tid] = mk4<R>(R(1) - R(2) * t, r * t * t, -m * t, R(0));
+        const R inv = r > R(0) ? R(1) / r : R(0);
+        const R ux = x * inv, uy = y * inv, uz = z * inv;
+        const R uu = ux * ux + uy * uy + uz * uz;
+        R C[3][LM + 1], S[3][LM + 1];
+        angular_levels<R, 0, LM, false>(C, S, ux, uy, uz, uu, LM, Ys, T, tid);
+    };
 
-    V4 cur = mk4<R>(R(0), R(0), R(0), R(0));
-    {
-        const int64_t gi = (int64_t)blockIdx.x * T + tid;
-        if (blockIdx.x < p.ntiles && gi < p.N) cur = ld4(posm + gi);
-    }
-    int since = 0;
-    for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x) {
-        // ---- phase 1: one particle per thread -> angular basis + radial seeds
-        {
-            R x = R(0), y = R(0), z = R(0), m = R(0);
-            if (finite4(cur.x, cur.y, cur.z, cur.w)) { x = cur.x; y = cur.y; z = cur.z; m = cur.w; }
-            else report(p.err, ETICS_ERR_NONFINITE);
-            const R r = sqrt(x * x + y * y + z * z);
-            const R t = R(1) / (R(1) + r);
-            s_rad[tid] = mk4<R>(R(1) - R(2) * t, r * t * t, -m * t, R(0));
-            const R inv = r > R(0) ? R(1) / r : R(0);
-            const R ux = x * inv, uy = y * inv, uz = z * inv;
-            const R uu = ux * ux + uy * uy + uz * uz;
-            R C[3][LM + 1], S[3][LM + 1];
-            angular_levels<R, 0, LM, false>(C, S, ux, uy, uz, uu, LM, Ys, T, tid);
+    V4 cur = load(blockIdx.x);
+    if (blockIdx.x < p.ntiles) basis(cur, s_rad0, Ys0);
+    cur = load(blockIdx.x + gridDim.x);
+    __syncthreads();
+    int since = 0, buf = 0;
+    for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x, buf ^= 1) {
+        // basis of the next tile into the other buffer (its last reader, the
+        // contraction of the previous tile, finished before the last barrier)
+        const int nxt = tile + gridDim.x;
+        if (nxt < p.ntiles) {
+            basis(cur, buf ? s_rad0 : s_rad1, buf ? Ys0 : Ys1);
+            cur = load(nxt + gridDim.x);
         }
-        {
-            const int nxt = tile + gridDim.x;
-            const int64_t gi = (int64_t)nxt * T + tid;
-            cur = (nxt < p.ntiles && gi < p.N) ? ld4(posm + gi) : mk4<R>(R(0), R(0), R(0), R(0));
-        }
-        __syncthreads();
-        // ---- phase 2: each warp accumulates its bin over the tile's particles
-        bin_dispatch<R, NR, LM, 0>(warp, acc, Ys, s_rad, T, lane);
+        // phase 2: each warp accumulates its bin over this tile's particles
+        bin_dispatch<R, NR, LM, 0>(warp, acc, buf ? Ys1 : Ys0, buf ? s_rad1 : s_rad0, T, lane);
         __syncthreads();
         if (++since == kBinFlushTiles) { flush(); since = 0; }
     }
@@ -276,8 +284,8 @@ inline int scf_coeffs_bins_launch(const void* posm, int64_t N, double* coeffs, v
     if (grid > ntiles) grid = ntiles > 0 ? ntiles : 1;
     ScfBinParams p{posm, N, ntiles, reinterpret_cast<double*>(ws), ctx.err};
     constexpr int NOUT = NB * NR * kBinCap;
-    constexpr size_t smem = ((NOUT * sizeof(double) + 15) / 16) * 16 + T * sizeof(Vec4<R>) +
-                            (size_t)(LM + 1) * (LM + 1) * T * sizeof(R);
+    constexpr size_t smem = ((NOUT * sizeof(double) + 15) / 16) * 16 +
+                            2 * (T * sizeof(Vec4<R>) + (size_t)(LM + 1) * (LM + 1) * T * sizeof(R));
     int nblocks = 0;
     if (ntiles > 0) {
         auto k = scf_coeff_bins_kernel<R, NR, LM>;
