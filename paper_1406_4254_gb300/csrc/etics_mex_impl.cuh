@@ -355,47 +355,35 @@ mex_pass2_kernel(const Vec4<R>* __restrict__ sorted, const uint32_t* __restrict_
         if (c < kMexNC) s_q0[cc] = (R)ldexp(v, -l * e);
         else s_p0[cc] = (R)ldexp(v, (l + 1) * e);
     }
-    // thread sums of the inner and outer moments of its kMexP particles, as
-    // pass 1 computed them (same particles, order and rounding)
-    R a[kMexNC], b[kMexNC];
-    {
-        const R* ts = thread_sums + (size_t)blockIdx.x * 2 * kMexNC * kMexThreads + tid;
+    // Inner moments first: this thread's sums over its kMexP particles (as
+    // pass 1 computed them: same particles, order and rounding), their
+    // exclusive prefix over the threads before it, then the forward sweep.
+    // The outer sums are loaded and scanned only after that sweep, so the two
+    // 49-component arrays are never live at the same time.
+    const R* ts = thread_sums + (size_t)blockIdx.x * 2 * kMexNC * kMexThreads + tid;
+    R a[kMexNC];
 #pragma unroll
-        for (int c = 0; c < kMexNC; ++c) {
-            a[c] = ts[(size_t)c * kMexThreads];
-            b[c] = ts[(size_t)(kMexNC + c) * kMexThreads];
-        }
-    }
-    // inner sums: exclusive prefix before this thread; outer sums: exclusive
-    // suffix after it (a true suffix sum, never total minus prefix)
+    for (int c = 0; c < kMexNC; ++c) a[c] = ts[(size_t)c * kMexThreads];
 #pragma unroll
     for (int c = 0; c < kMexNC; ++c) {
-        R x = a[c], y = b[c];
+        R x = a[c];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const R tx = __shfl_up_sync(0xffffffffu, x, o);
-            const R ty = __shfl_down_sync(0xffffffffu, y, o);
             if (lane >= o) x += tx;
-            if (lane + o < 32) y += ty;
         }
         if (lane == 31) s_wq[warp][c] = x;
-        if (lane == 0) s_wp[warp][c] = y;
         const R ex = __shfl_up_sync(0xffffffffu, x, 1);
-        const R ey = __shfl_down_sync(0xffffffffu, y, 1);
         a[c] = (lane == 0) ? R(0) : ex;
-        b[c] = (lane == 31) ? R(0) : ey;
     }
     __syncthreads();
 #pragma unroll
     for (int c = 0; c < kMexNC; ++c) {
-        R q0 = s_q0[c], p0 = s_p0[c];
+        R q0 = s_q0[c];
         for (int w = 0; w < warp; ++w) q0 += s_wq[w][c];
-        for (int w = NW - 1; w > warp; --w) p0 += s_wp[w][c];
         a[c] = q0 + a[c];
-        b[c] = p0 + b[c];
     }
-    // forward sweep (inner part of the field, kept in shared memory), then the
-    // reverse sweep (outer part) which completes and scatters each particle
+    // forward sweep: inner part of the field, kept in shared memory
 #pragma unroll 1
     for (int k = 0; k < kMexP; ++k) {
         MexParticle<R> pt;
@@ -405,6 +393,31 @@ mex_pass2_kernel(const Vec4<R>* __restrict__ sorted, const uint32_t* __restrict_
         R pot = R(0), ax = R(0), ay = R(0), az = R(0);
         mex_fwd<R, 0, ACC>(C, S, pt, l_max, pt.m, irho, irho, a, pot, ax, ay, az);
         st4(&s_f[k * kMexThreads + tid], mk4<R>(ax, ay, az, pot));
+    }
+    // outer sums: exclusive suffix after this thread (a true suffix sum,
+    // never total minus prefix), then the reverse sweep which completes and
+    // scatters each particle
+    R b[kMexNC];
+#pragma unroll
+    for (int c = 0; c < kMexNC; ++c) b[c] = ts[(size_t)(kMexNC + c) * kMexThreads];
+#pragma unroll
+    for (int c = 0; c < kMexNC; ++c) {
+        R y = b[c];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const R ty = __shfl_down_sync(0xffffffffu, y, o);
+            if (lane + o < 32) y += ty;
+        }
+        if (lane == 0) s_wp[warp][c] = y;
+        const R ey = __shfl_down_sync(0xffffffffu, y, 1);
+        b[c] = (lane == 31) ? R(0) : ey;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < kMexNC; ++c) {
+        R p0 = s_p0[c];
+        for (int w = NW - 1; w > warp; --w) p0 += s_wp[w][c];
+        b[c] = p0 + b[c];
     }
     const R s1 = scale, s2 = scale * scale;
 #pragma unroll 1
