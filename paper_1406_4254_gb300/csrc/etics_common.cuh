@@ -332,6 +332,34 @@ __host__ __device__ __forceinline__ int col_offset(int l) {
 __host__ __device__ __forceinline__ int col_total(int lmax) { return col_offset(lmax + 1); }
 
 // launch context handed from the C ABI to the kernel launchers
+// Programmatic dependent launch.  A kernel started by launch_pdl may be
+// scheduled while the previous kernel in its stream drains (its launch
+// latency overlaps the predecessor's tail); it must execute pdl_wait()
+// (griddepcontrol.wait: returns once every prerequisite grid has completed
+// and its memory is visible) before it touches global memory that the
+// predecessor reads or writes.  No kernel triggers its dependents
+// explicitly: the implicit trigger at block exit keeps waiting blocks from
+// holding SM slots that a concurrent stream could use.  pdl_wait() is a
+// no-op in a kernel launched the ordinary way.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t stream, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, args...);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 struct LaunchCtx {
     cudaStream_t stream;
     unsigned* err;        // device error word

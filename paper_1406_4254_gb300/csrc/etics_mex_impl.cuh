@@ -209,6 +209,7 @@ mex_pass1_kernel(const Vec4<R>* __restrict__ posm, const uint32_t* __restrict__ 
                  R* __restrict__ thread_sums, unsigned* err) {
     __shared__ Vec4<R> s_pt[kMexTile];
     __shared__ R s_red[kMexThreads / 32][2 * kMexNC];
+    pdl_wait();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t base = (int64_t)blockIdx.x * kMexTile;
     const int64_t rem = N - base;
@@ -292,6 +293,7 @@ constexpr int kCarryThreads = 1024;
 static __global__ void __launch_bounds__(kCarryThreads)
 mex_carry_kernel(const double* __restrict__ tile_agg, int ntiles, double* __restrict__ carry) {
     __shared__ double s_w[kCarryThreads / 32];
+    pdl_wait();
     const int c = blockIdx.x;
     const bool rev = c >= kMexNC;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -334,6 +336,7 @@ mex_pass2_kernel(const Vec4<R>* __restrict__ sorted, const uint32_t* __restrict_
     __shared__ Vec4<R> s_f[kMexTile];   // inner part of each particle's field
     __shared__ R s_q0[kMexNC], s_p0[kMexNC];
     __shared__ R s_wq[NW][kMexNC], s_wp[NW][kMexNC];
+    pdl_wait();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t base = (int64_t)blockIdx.x * kMexTile;
     const int64_t rem = N - base;
@@ -493,23 +496,25 @@ inline int mex_field_impl(const void* posm, int64_t N, int l_max, void* out, int
     stage_event(ctx, 2);
     const int nt = mex_tiles(N);
     const Vec4<R>* pp = reinterpret_cast<const Vec4<R>*>(posm);
-    mex_pass1_kernel<R><<<nt, kMexThreads, 0, ctx.stream>>>(pp, b.sort.vals_a, N, l_max, b.sorted,
-                                                            b.tile_agg, b.thread_sums, ctx.err);
-    if (cudaGetLastError()) return ETICS_ERR_CUDA;
+    if (launch_pdl(mex_pass1_kernel<R>, dim3(nt), dim3(kMexThreads), 0, ctx.stream, pp,
+                   (const uint32_t*)b.sort.vals_a, N, l_max, b.sorted, b.tile_agg, b.thread_sums, ctx.err))
+        return ETICS_ERR_CUDA;
     ++*ctx.launches;
     stage_event(ctx, 3);
-    mex_carry_kernel<<<2 * kMexNC, kCarryThreads, 0, ctx.stream>>>(b.tile_agg, nt, b.carry);
-    if (cudaGetLastError()) return ETICS_ERR_CUDA;
+    if (launch_pdl(mex_carry_kernel, dim3(2 * kMexNC), dim3(kCarryThreads), 0, ctx.stream,
+                   (const double*)b.tile_agg, nt, b.carry))
+        return ETICS_ERR_CUDA;
     ++*ctx.launches;
     stage_event(ctx, 4);
     Vec4<R>* op = reinterpret_cast<Vec4<R>*>(out);
-    if (out_mask & ETICS_OUT_ACC)
-        mex_pass2_kernel<R, true><<<nt, kMexThreads, 0, ctx.stream>>>(
-            b.sorted, b.sort.vals_a, N, l_max, b.carry, b.thread_sums, op, out_mask, ctx.err);
-    else
-        mex_pass2_kernel<R, false><<<nt, kMexThreads, 0, ctx.stream>>>(
-            b.sorted, b.sort.vals_a, N, l_max, b.carry, b.thread_sums, op, out_mask, ctx.err);
-    if (cudaGetLastError()) return ETICS_ERR_CUDA;
+    const cudaError_t le = (out_mask & ETICS_OUT_ACC)
+        ? launch_pdl(mex_pass2_kernel<R, true>, dim3(nt), dim3(kMexThreads), 0, ctx.stream,
+                     (const Vec4<R>*)b.sorted, (const uint32_t*)b.sort.vals_a, N, l_max,
+                     (const double*)b.carry, (const R*)b.thread_sums, op, out_mask, ctx.err)
+        : launch_pdl(mex_pass2_kernel<R, false>, dim3(nt), dim3(kMexThreads), 0, ctx.stream,
+                     (const Vec4<R>*)b.sorted, (const uint32_t*)b.sort.vals_a, N, l_max,
+                     (const double*)b.carry, (const R*)b.thread_sums, op, out_mask, ctx.err);
+    if (le) return ETICS_ERR_CUDA;
     ++*ctx.launches;
     stage_event(ctx, 5);
     return ETICS_OK;

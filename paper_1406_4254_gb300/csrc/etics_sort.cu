@@ -4,11 +4,14 @@
 //
 // GB300 design: a hand-written stable LSD radix sort (4 passes of 8 bits) of
 // the high 32 bits of the FP64 r^2 bit pattern, one kernel per pass
-// ("one-sweep": per-tile digit ranking with warp match + a decoupled
-// lookback over tiles for the digit offsets, scatter staged through shared
-// memory for coalesced writes).  Runs of equal high words are then ordered by
-// the low 32 bits and the particle index, which reproduces the exact FP64
-// order (r^2 = (x*x + y*y) + z*z rounded as a CPU does, ties by index).
+// ("one-sweep": per-tile digit ranking with warp ballots, the tile's keys
+// placed in digit order in shared memory, a decoupled lookback over tiles for
+// the digit offsets, coalesced writes of digit runs).  Runs of equal high
+// words are then ordered by the low 32 bits and the particle index, which
+// reproduces the exact FP64 order (r^2 = (x*x + y*y) + z*z rounded as a CPU
+// does, ties by index).  The passes and the tie fix-up are launched with
+// programmatic dependent launch, so each launch overlaps its predecessor's
+// tail.
 #include "etics_internal.h"
 
 namespace etics {
@@ -17,6 +20,8 @@ constexpr int kSortThreads = 256;
 constexpr int kSortKpt = 16;
 constexpr int kSortTile = kSortThreads * kSortKpt;   // 4096 keys per tile
 constexpr int kLookbackWindow = 32;
+constexpr int kStatusPad = kLookbackWindow;   // zeroed tiles before tile 0
+constexpr int kMatchDigits = 8;               // rank with match_any up to this many digits
 constexpr uint32_t kCountMask = (1u << 30) - 1;
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagInc = 2u << 30;
@@ -163,23 +168,6 @@ int radial_keys_impl(const void* posm, int64_t N, uint32_t* keys, const LaunchCt
 template int radial_keys_impl<float>(const void*, int64_t, uint32_t*, const LaunchCtx&);
 template int radial_keys_impl<double>(const void*, int64_t, uint32_t*, const LaunchCtx&);
 
-// exclusive scan over the 256 threads of a block (one value per thread)
-__device__ __forceinline__ uint32_t block_excl_scan256(uint32_t v, uint32_t* s_warp) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += t;
-    }
-    if (lane == 31) s_warp[warp] = x;
-    __syncthreads();
-    uint32_t base = 0;
-    for (int w = 0; w < warp; ++w) base += s_warp[w];
-    __syncthreads();
-    return base + x - v;
-}
-
 __device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) {
     return *reinterpret_cast<const volatile uint32_t*>(p);
 }
@@ -187,6 +175,51 @@ __device__ __forceinline__ void st_volatile(uint32_t* p, uint32_t v) {
     *reinterpret_cast<volatile uint32_t*>(p) = v;
 }
 
+// Stable rank of every key among the equal digits of its warp, keys taken in
+// tile order (slot s, then lane).  The lanes that share a digit are found
+// either with __match_any_sync (fast when a warp holds few distinct digits)
+// or with one ballot per digit bit plus one for validity (a cost independent
+// of how many distinct digits there are).
+template <bool kMatch>
+__device__ __forceinline__ void rank_in_warp(const uint32_t (&d)[kSortKpt], uint32_t (&rank)[kSortKpt],
+                                             uint32_t* whist, int lane) {
+    const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+    for (int s = 0; s < kSortKpt; ++s) {
+        unsigned mask;
+        if (kMatch) {
+            mask = __match_any_sync(0xffffffffu, d[s]);
+        } else {
+            const unsigned vb = __ballot_sync(0xffffffffu, d[s] < 256u);
+            mask = d[s] < 256u ? vb : ~vb;
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const bool bit = (d[s] >> b) & 1u;
+                const unsigned bal = __ballot_sync(0xffffffffu, bit);
+                mask &= bit ? bal : ~bal;
+            }
+        }
+        const unsigned lower = mask & below;
+        uint32_t before = 0;
+        if (d[s] < 256u) before = whist[d[s]];
+        rank[s] = before + (uint32_t)__popc(lower);
+        __syncwarp();
+        if (d[s] < 256u && lower == 0u) whist[d[s]] = before + (uint32_t)__popc(mask);
+        __syncwarp();
+    }
+}
+
+// One pass of the stable LSD radix sort (8-bit digit at `shift`) over tiles
+// of kSortTile keys.  Order of work in a tile: load and rank; publish the
+// tile's digit counts (status word: flag | count); scan the global histogram
+// and the tile counts together; place the keys in digit order in shared
+// memory; then find the exclusive prefix of each digit over earlier tiles by
+// a decoupled lookback; finally write the keys out in digit runs.  `status`
+// holds kStatusPad zeroed (never published) tiles before tile 0, so a
+// lookback window may reach below tile 0 without a bounds test: tile 0
+// always publishes an inclusive prefix, which ends every walk first.
+// Launched with programmatic stream serialisation: nothing global is touched
+// before griddepcontrol.wait.
 __global__ void __launch_bounds__(kSortThreads, 2)
 onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                 uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
@@ -197,12 +230,16 @@ onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
     __shared__ uint32_t s_whist[kSortThreads / 32][256];
     __shared__ uint32_t s_dexcl[256];
     __shared__ uint32_t s_gbase[256];
-    __shared__ uint32_t s_scan[kSortThreads / 32];
+    __shared__ uint32_t s_scan[2][kSortThreads / 32];
     __shared__ uint32_t s_tile;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_tile = atomicAdd(counter, 1u);
     for (int i = tid; i < (kSortThreads / 32) * 256; i += kSortThreads) (&s_whist[0][0])[i] = 0;
-    __syncthreads();
+    pdl_wait();
+    if (tid == 0) s_tile = atomicAdd(counter, 1u);
+    const int dig = tid;
+    const uint32_t gcount = hist[dig];
+    // digits present in this pass over all keys: few -> rank with match_any
+    const int ndig = __syncthreads_count(gcount != 0u);
     const uint32_t tile = s_tile;
     const int64_t start = (int64_t)tile * kSortTile;
 
@@ -220,79 +257,35 @@ onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
             d[s] = 256u;   // not a digit: out of range
         }
     }
-    // stable rank of every key among equal digits of this warp, in key order
-#pragma unroll
-    for (int s = 0; s < kSortKpt; ++s) {
-        const unsigned mask = __match_any_sync(0xffffffffu, d[s]);
-        const unsigned lower = mask & ((1u << lane) - 1u);
-        uint32_t before = 0;
-        if (d[s] < 256u) before = s_whist[warp][d[s]];
-        rank[s] = before + (uint32_t)__popc(lower);
-        __syncwarp();
-        if (d[s] < 256u && lower == 0u) s_whist[warp][d[s]] = before + (uint32_t)__popc(mask);
-        __syncwarp();
-    }
+    if (ndig <= kMatchDigits) rank_in_warp<true>(d, rank, s_whist[warp], lane);
+    else rank_in_warp<false>(d, rank, s_whist[warp], lane);
     __syncthreads();
     // per digit (one thread each): offsets over warps and the tile count
-    const int dig = tid;
     uint32_t count = 0;
     for (int w = 0; w < kSortThreads / 32; ++w) {
         const uint32_t t = s_whist[w][dig];
         s_whist[w][dig] = count;
         count += t;
     }
-    // decoupled lookback over earlier tiles for this digit
-    uint32_t* st = status + (size_t)tile * 256;
-    uint32_t excl = 0;
-    const uint32_t gcount = hist[dig];
-    if (tile == 0 || gcount == 0u) {
-        // tile 0, or a digit no key has (nobody looks it up)
-        st_volatile(st + dig, kFlagInc | count);
-    } else {
-        st_volatile(st + dig, kFlagAgg | count);
-        // look back over a window of predecessors at once (independent loads),
-        // summing aggregates until an inclusive prefix is found; tile 0 always
-        // publishes an inclusive prefix, so the walk ends
-        int64_t t = (int64_t)tile - 1;
-        int spins = 0;
-        while (t >= 0) {
-            uint32_t w[kLookbackWindow];
+    // publish at once: tile 0 (and any digit no key has) as inclusive
+    uint32_t* st = status + (size_t)(tile + kStatusPad) * 256 + dig;
+    const bool lookback = tile != 0 && gcount != 0u;
+    st_volatile(st, (lookback ? kFlagAgg : kFlagInc) | count);
+    // exclusive scans of the global histogram (start of each digit) and of
+    // the tile counts (start of each digit in the tile), together
+    uint32_t xa = gcount, xb = count;
 #pragma unroll
-            for (int j = 0; j < kLookbackWindow; ++j)
-                w[j] = (t - j >= 0) ? ld_volatile(status + (size_t)(t - j) * 256 + dig) : 0u;
-            // consume the window in order up to the first inclusive prefix or
-            // the first predecessor that has not published yet (slots beyond
-            // tile 0 read as unpublished, and tile 0 is always inclusive)
-            int used;
-            bool done = false;
-            int first_inc = kLookbackWindow, first_wait = kLookbackWindow;
-#pragma unroll
-            for (int j = kLookbackWindow - 1; j >= 0; --j) {
-                const uint32_t flag = w[j] & ~kCountMask;
-                if (flag == 0u) first_wait = j;
-                if (flag == kFlagInc) first_inc = j;
-            }
-            if (first_inc < first_wait) { used = first_inc + 1; done = true; }
-            else used = first_wait;
-            if (used > t + 1) used = (int)(t + 1);
-#pragma unroll
-            for (int j = 0; j < kLookbackWindow; ++j)
-                if (j < used) excl += w[j] & kCountMask;
-            if (done) break;
-            t -= used;
-            const bool wait = used < kLookbackWindow && t >= 0;
-            if (wait) {
-                if (++spins > kSpinLimit) { report(err, ETICS_ERR_TIMEOUT); break; }
-                __nanosleep(32);
-            }
-        }
-        st_volatile(st + dig, kFlagInc | (excl + count));
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t ta = __shfl_up_sync(0xffffffffu, xa, o);
+        const uint32_t tb = __shfl_up_sync(0xffffffffu, xb, o);
+        if (lane >= o) { xa += ta; xb += tb; }
     }
-    // global start of each digit: exclusive scan of this pass's histogram
-    const uint32_t hexcl = block_excl_scan256(hist[dig], s_scan);
-    const uint32_t dexcl = block_excl_scan256(count, s_scan);
-    s_dexcl[dig] = dexcl;
-    s_gbase[dig] = hexcl + excl;
+    if (lane == 31) { s_scan[0][warp] = xa; s_scan[1][warp] = xb; }
+    __syncthreads();
+    uint32_t ba = 0, bb = 0;
+    for (int w = 0; w < warp; ++w) { ba += s_scan[0][w]; bb += s_scan[1][w]; }
+    const uint32_t hexcl = ba + xa - gcount;
+    s_dexcl[dig] = bb + xb - count;
     __syncthreads();
 #pragma unroll
     for (int s = 0; s < kSortKpt; ++s) {
@@ -302,15 +295,68 @@ onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
             s_vals[pos] = v[s];
         }
     }
+    // decoupled lookback over earlier tiles for this digit: a window of
+    // predecessors is read at once; flags become bit masks; counts are summed
+    // up to the first inclusive prefix, or up to the first predecessor that
+    // has not published (then that one word is polled before the next window)
+    uint32_t excl = 0;
+    if (lookback) {
+        const uint32_t* p = st - 256;   // tile - 1
+        int spins = 0;
+        for (;;) {
+            uint32_t w[kLookbackWindow];
+#pragma unroll
+            for (int j = 0; j < kLookbackWindow; ++j) w[j] = ld_volatile(p - j * 256);
+            uint32_t pub = 0, inc = 0;
+#pragma unroll
+            for (int j = 0; j < kLookbackWindow; ++j) {
+                const uint32_t f = w[j] >> 30;
+                pub |= (f != 0u ? 1u : 0u) << j;
+                inc |= (f == (kFlagInc >> 30) ? 1u : 0u) << j;
+            }
+            const int first_wait = ~pub ? __ffs(~pub) - 1 : kLookbackWindow;
+            const int first_inc = inc ? __ffs(inc) - 1 : kLookbackWindow;
+            const bool done = first_inc < first_wait;
+            const int used = done ? first_inc + 1 : first_wait;
+            const uint32_t take = used >= 32 ? 0xffffffffu : ((1u << used) - 1u);
+#pragma unroll
+            for (int j = 0; j < kLookbackWindow; ++j)
+                if ((take >> j) & 1u) excl += w[j] & kCountMask;
+            if (done) break;
+            p -= (size_t)used * 256;
+            if (used < kLookbackWindow) {
+                bool timed_out = false;
+                while ((ld_volatile(p) >> 30) == 0u) {
+                    if (++spins > kSpinLimit) { timed_out = true; break; }
+                    __nanosleep(32);
+                }
+                if (timed_out) { report(err, ETICS_ERR_TIMEOUT); break; }
+            }
+        }
+        st_volatile(st, kFlagInc | (excl + count));
+    }
+    s_gbase[dig] = hexcl + excl;
     __syncthreads();
     const int64_t rem = N - start;
     const int nvalid = (int)(rem < kSortTile ? rem : kSortTile);
-    for (int i = tid; i < nvalid; i += kSortThreads) {
-        const uint32_t kk = s_keys[i];
-        const uint32_t dd = (kk >> shift) & 255u;
-        const uint32_t pos = s_gbase[dd] + (uint32_t)i - s_dexcl[dd];
-        keys_out[pos] = kk;
-        vals_out[pos] = s_vals[i];
+    if (nvalid == kSortTile) {
+#pragma unroll
+        for (int s = 0; s < kSortKpt; ++s) {
+            const int i = tid + s * kSortThreads;
+            const uint32_t kk = s_keys[i];
+            const uint32_t dd = (kk >> shift) & 255u;
+            const uint32_t pos = s_gbase[dd] + (uint32_t)i - s_dexcl[dd];
+            keys_out[pos] = kk;
+            vals_out[pos] = s_vals[i];
+        }
+    } else {
+        for (int i = tid; i < nvalid; i += kSortThreads) {
+            const uint32_t kk = s_keys[i];
+            const uint32_t dd = (kk >> shift) & 255u;
+            const uint32_t pos = s_gbase[dd] + (uint32_t)i - s_dexcl[dd];
+            keys_out[pos] = kk;
+            vals_out[pos] = s_vals[i];
+        }
     }
 }
 
@@ -381,6 +427,7 @@ tie_fixup_kernel(const uint32_t* __restrict__ key, const Vec4<R>* __restrict__ p
     const int64_t rem = N - base;
     const int nt = (int)(rem < kFixTile ? rem : kFixTile);
     if (threadIdx.x == 0) s_nruns = 0;
+    pdl_wait();
     // s_key[i + 1] = key[base + i] for i in [-1, nt]; sentinels outside [0, N)
     for (int i = threadIdx.x - 1; i <= nt; i += kFixThreads) {
         const int64_t g = base + i;
@@ -429,12 +476,12 @@ SortBuffers sort_buffers(void* ws, int64_t N, size_t* total) {
     b.vals_a = reinterpret_cast<uint32_t*>(take(n4));
     b.vals_b = reinterpret_cast<uint32_t*>(take(n4));
     const size_t nst = (size_t)sort_tiles(N);
-    b.zero_bytes = (4 * 256 + 4 * nst * 256 + 64) * 4;
+    b.zero_bytes = (4 * 256 + 4 * (nst + kStatusPad) * 256 + 64) * 4;
     b.zero_bytes = (b.zero_bytes + 255) / 256 * 256;
     uint8_t* z = take(b.zero_bytes);
     b.hist = reinterpret_cast<uint32_t*>(z);
     b.status = b.hist ? b.hist + 4 * 256 : nullptr;
-    b.counters = b.status ? b.status + 4 * nst * 256 : nullptr;
+    b.counters = b.status ? b.status + 4 * (nst + kStatusPad) * 256 : nullptr;
     b.zero_base = z;
     if (total) *total = off;
     return b;
@@ -454,19 +501,21 @@ int radial_sort_impl(const void* posm, int64_t N, const SortBuffers& b, const La
     const int nst = sort_tiles(N);
     uint32_t *kin = b.keys_a, *vin = b.vals_a, *kout = b.keys_b, *vout = b.vals_b;
     for (int pass = 0; pass < 4; ++pass) {
-        onesweep_kernel<<<nst, kSortThreads, 0, ctx.stream>>>(
-            kin, pass == 0 ? nullptr : vin, kout, vout, b.hist + pass * 256,
-            b.status + (size_t)pass * nst * 256, b.counters + pass, 8 * pass, N, ctx.err);
-        if (cudaGetLastError()) return ETICS_ERR_CUDA;
+        const uint32_t* vals_in = pass == 0 ? nullptr : vin;
+        if (launch_pdl(onesweep_kernel, dim3(nst), dim3(kSortThreads), 0, ctx.stream, (const uint32_t*)kin,
+                       vals_in, kout, vout, (const uint32_t*)(b.hist + pass * 256),
+                       b.status + (size_t)pass * (nst + kStatusPad) * 256, b.counters + pass, 8 * pass,
+                       N, ctx.err))
+            return ETICS_ERR_CUDA;
         ++*ctx.launches;
         uint32_t* t = kin; kin = kout; kout = t;
         t = vin; vin = vout; vout = t;
     }
     // after 4 passes the sorted keys/values are back in keys_a / vals_a
     const int fg = (int)((N + kFixTile - 1) / kFixTile);
-    tie_fixup_kernel<R><<<fg, kFixThreads, 0, ctx.stream>>>(
-        b.keys_a, reinterpret_cast<const Vec4<R>*>(posm), b.vals_a, N, ctx.err);
-    if (cudaGetLastError()) return ETICS_ERR_CUDA;
+    if (launch_pdl(tie_fixup_kernel<R>, dim3(fg), dim3(kFixThreads), 0, ctx.stream,
+                   (const uint32_t*)b.keys_a, reinterpret_cast<const Vec4<R>*>(posm), b.vals_a, N, ctx.err))
+        return ETICS_ERR_CUDA;
     ++*ctx.launches;
     return ETICS_OK;
 }
