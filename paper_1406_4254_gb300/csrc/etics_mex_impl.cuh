@@ -10,14 +10,16 @@
 //   pass 1  gathers the particles in radial order (sorted copy), and reduces
 //           each tile's moments m rho^l Y and m rho^-(l+1) Y (rho = r / s_t,
 //           s_t a power of two per tile, so FP32 never overflows) to FP64.
-//           It also stores each thread's sums over its kMexP particles.
+//           It also scans each thread's sums over its kMexP particles inside
+//           the tile and stores every thread's exclusive prefix (inner) and
+//           suffix (outer).
 //   carry   scans the per-tile FP64 sums in a fixed order: exclusive forward
 //           for the inner moments, exclusive reverse (a true suffix sum) for
 //           the outer ones -- deterministic.
-//   pass 2  scans those thread sums inside the tile (warp shuffles + shared
-//           memory, forward and reverse), evaluates the field at every
-//           particle from the exclusive q and p in a forward and a reverse
-//           sweep, and scatters (a, Phi) back to the caller's order.
+//   pass 2  adds the tile carry to those per-thread prefixes and suffixes,
+//           evaluates the field at every particle from the exclusive q and p
+//           in a forward and a reverse sweep, and scatters (a, Phi) back to
+//           the caller's order.
 // All harmonics are the unnormalised Cartesian solid harmonics of
 // etics_common.cuh; the MEX weights (l-m)!/(l+m)! (x2 for m > 0) restore the
 // orthonormal normalisation and the 4pi/(2l+1) factor at once.
@@ -73,9 +75,6 @@ struct MexParticle {
     }
 };
 
-__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
-
 // moment of column c of level L: index L*L + c
 template <typename R, int L>
 __device__ __forceinline__ R harm_col(const R* C, const R* S, int c) {
@@ -94,10 +93,8 @@ __device__ __forceinline__ void mex_moments(R (&C)[3][kMexLB + 1], R (&S)[3][kMe
 #pragma unroll
         for (int c = 0; c <= 2 * L; ++c) {
             const R y = harm_col<R, L>(C[s0], S[s0], c);
-            // separately rounded products: the reverse sweep subtracts exactly
-            // these values again
-            ain[L * L + c] += mul_rn(win, y);
-            aout[L * L + c] += mul_rn(wout, y);
+            ain[L * L + c] = fma(win, y, ain[L * L + c]);
+            aout[L * L + c] = fma(wout, y, aout[L * L + c]);
         }
         mex_moments<R, L + 1>(C, S, pt, l_max, win * pt.rho, wout * irho, irho, ain, aout);
     }
@@ -153,7 +150,7 @@ __device__ __forceinline__ void mex_fwd(R (&C)[3][kMexLB + 1], R (&S)[3][kMexLB 
         }
 #pragma unroll
         for (int c = 0; c <= 2 * L; ++c)
-            q[L * L + c] += mul_rn(win, harm_col<R, L>(C[s0], S[s0], c));
+            q[L * L + c] = fma(win, harm_col<R, L>(C[s0], S[s0], c), q[L * L + c]);
         mex_fwd<R, L + 1, ACC>(C, S, pt, l_max, win * pt.rho, rinv * irho, irho, q, pot, ax, ay, az);
     }
 }
@@ -193,10 +190,44 @@ __device__ __forceinline__ void mex_rev(R (&C)[3][kMexLB + 1], R (&S)[3][kMexLB 
         }
 #pragma unroll
         for (int c = 0; c <= 2 * L; ++c)
-            p[L * L + c] += mul_rn(wout, harm_col<R, L>(C[s0], S[s0], c));
+            p[L * L + c] = fma(wout, harm_col<R, L>(C[s0], S[s0], c), p[L * L + c]);
         mex_rev<R, L + 1, ACC>(C, S, pt, l_max, wout * irho, rl * pt.rho, rl, irho, p, pot, ax,
                                ay, az);
     }
+}
+
+// Exclusive scan over the 32 lanes of a warp of each of the kMexNC components
+// in v (forward: prefix in lane order; backward: suffix), in two rounds of at
+// most kMexScanHalf components.  buf: the warp's 32 x kMexScanHalf slots (row
+// = lane; the odd row length keeps both access patterns free of bank
+// conflicts).  total[c] receives the warp's sum of component c.
+constexpr int kMexScanHalf = (kMexNC + 1) / 2;
+static_assert(kMexScanHalf % 2 == 1, "row length must be odd");
+template <typename R, bool kForward, int C0, int NC>
+__device__ __forceinline__ void scan_rows_part(R (&v)[kMexNC], R* buf, R* total, int lane) {
+#pragma unroll
+    for (int j = 0; j < NC; ++j) buf[lane * kMexScanHalf + j] = v[C0 + j];
+    __syncwarp();
+    if (lane < NC) {
+        R run = R(0);
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+            const int r = kForward ? t : 31 - t;
+            const R x = buf[r * kMexScanHalf + lane];
+            buf[r * kMexScanHalf + lane] = run;
+            run += x;
+        }
+        total[C0 + lane] = run;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < NC; ++j) v[C0 + j] = buf[lane * kMexScanHalf + j];
+    __syncwarp();
+}
+template <typename R, bool kForward>
+__device__ __forceinline__ void scan_rows(R (&v)[kMexNC], R* buf, R* total, int lane) {
+    scan_rows_part<R, kForward, 0, kMexScanHalf>(v, buf, total, lane);
+    scan_rows_part<R, kForward, kMexScanHalf, kMexNC - kMexScanHalf>(v, buf, total, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -251,27 +282,30 @@ mex_pass1_kernel(const Vec4<R>* __restrict__ posm, const uint32_t* __restrict__ 
         pt.init(s_pt[k * kMexThreads + tid], scale);
         particle_moments<R>(pt, l_max, ain, aout);
     }
-    // this thread's inner and outer sums for pass 2 (component-major, so the
-    // stores of a warp are contiguous)
+    // in-tile scans of the thread sums, per component: exclusive prefix
+    // (inner) and suffix (outer) over the lanes of each warp, transposed
+    // through shared memory: every thread writes its row of sums, each lane
+    // scans one component serially down the 32 rows (in lane order), every
+    // thread reads its row back.  Half of the components per round.  The
+    // warp totals go to s_red for the tile sums and the block-level combine.
+    // The rows live where the particles were (s_pt is no longer read).
+    static_assert(kMexThreads / 32 * 32 * kMexScanHalf * sizeof(R) <= sizeof(s_pt), "scan rows");
+    __syncthreads();
+    R* rows = reinterpret_cast<R*>(s_pt) + warp * 32 * kMexScanHalf;
+    scan_rows<R, true>(ain, rows, &s_red[warp][0], lane);
+    scan_rows<R, false>(aout, rows, &s_red[warp][kMexNC], lane);
+    __syncthreads();
     {
         R* ts = thread_sums + (size_t)blockIdx.x * 2 * kMexNC * kMexThreads + tid;
 #pragma unroll
         for (int c = 0; c < kMexNC; ++c) {
-            ts[(size_t)c * kMexThreads] = ain[c];
-            ts[(size_t)(kMexNC + c) * kMexThreads] = aout[c];
+            R q = R(0), p = R(0);
+            for (int w = 0; w < warp; ++w) q += s_red[w][c];
+            for (int w = kMexThreads / 32 - 1; w > warp; --w) p += s_red[w][kMexNC + c];
+            ts[(size_t)c * kMexThreads] = q + ain[c];
+            ts[(size_t)(kMexNC + c) * kMexThreads] = p + aout[c];
         }
     }
-#pragma unroll
-    for (int c = 0; c < kMexNC; ++c) {
-        R a = ain[c], b = aout[c];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_xor_sync(0xffffffffu, a, o);
-            b += __shfl_xor_sync(0xffffffffu, b, o);
-        }
-        if (lane == 0) { s_red[warp][c] = a; s_red[warp][kMexNC + c] = b; }
-    }
-    __syncthreads();
     for (int c = tid; c < 2 * kMexNC; c += kMexThreads) {
         double s = 0.0;
         for (int w = 0; w < kMexThreads / 32; ++w) s += (double)s_red[w][c];
@@ -331,11 +365,9 @@ __global__ void __launch_bounds__(kMexThreads, 4)
 mex_pass2_kernel(const Vec4<R>* __restrict__ sorted, const uint32_t* __restrict__ perm, int64_t N,
                  int l_max, const double* __restrict__ carry, const R* __restrict__ thread_sums,
                  Vec4<R>* __restrict__ out, int out_mask, unsigned* err) {
-    constexpr int NW = kMexThreads / 32;
     __shared__ Vec4<R> s_pt[kMexTile];
     __shared__ Vec4<R> s_f[kMexTile];   // inner part of each particle's field
     __shared__ R s_q0[kMexNC], s_p0[kMexNC];
-    __shared__ R s_wq[NW][kMexNC], s_wp[NW][kMexNC];
     pdl_wait();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t base = (int64_t)blockIdx.x * kMexTile;
@@ -358,34 +390,15 @@ mex_pass2_kernel(const Vec4<R>* __restrict__ sorted, const uint32_t* __restrict_
         if (c < kMexNC) s_q0[cc] = (R)ldexp(v, -l * e);
         else s_p0[cc] = (R)ldexp(v, (l + 1) * e);
     }
-    // Inner moments first: this thread's sums over its kMexP particles (as
-    // pass 1 computed them: same particles, order and rounding), their
-    // exclusive prefix over the threads before it, then the forward sweep.
-    // The outer sums are loaded and scanned only after that sweep, so the two
-    // 49-component arrays are never live at the same time.
+    __syncthreads();
+    // exclusive inner sum before this thread's first particle: the tile's
+    // carry plus this thread's in-tile prefix (pass 1); the outer sums are
+    // loaded only after the forward sweep, so the two 49-component arrays
+    // are never live at the same time
     const R* ts = thread_sums + (size_t)blockIdx.x * 2 * kMexNC * kMexThreads + tid;
     R a[kMexNC];
 #pragma unroll
-    for (int c = 0; c < kMexNC; ++c) a[c] = ts[(size_t)c * kMexThreads];
-#pragma unroll
-    for (int c = 0; c < kMexNC; ++c) {
-        R x = a[c];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const R tx = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += tx;
-        }
-        if (lane == 31) s_wq[warp][c] = x;
-        const R ex = __shfl_up_sync(0xffffffffu, x, 1);
-        a[c] = (lane == 0) ? R(0) : ex;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int c = 0; c < kMexNC; ++c) {
-        R q0 = s_q0[c];
-        for (int w = 0; w < warp; ++w) q0 += s_wq[w][c];
-        a[c] = q0 + a[c];
-    }
+    for (int c = 0; c < kMexNC; ++c) a[c] = s_q0[c] + ts[(size_t)c * kMexThreads];
     // forward sweep: inner part of the field, kept in shared memory
 #pragma unroll 1
     for (int k = 0; k < kMexP; ++k) {
@@ -397,31 +410,12 @@ mex_pass2_kernel(const Vec4<R>* __restrict__ sorted, const uint32_t* __restrict_
         mex_fwd<R, 0, ACC>(C, S, pt, l_max, pt.m, irho, irho, a, pot, ax, ay, az);
         st4(&s_f[k * kMexThreads + tid], mk4<R>(ax, ay, az, pot));
     }
-    // outer sums: exclusive suffix after this thread (a true suffix sum,
-    // never total minus prefix), then the reverse sweep which completes and
-    // scatters each particle
+    // exclusive outer sum after this thread's last particle (a true suffix
+    // sum, never total minus prefix), then the reverse sweep which completes
+    // and scatters each particle
     R b[kMexNC];
 #pragma unroll
-    for (int c = 0; c < kMexNC; ++c) b[c] = ts[(size_t)(kMexNC + c) * kMexThreads];
-#pragma unroll
-    for (int c = 0; c < kMexNC; ++c) {
-        R y = b[c];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const R ty = __shfl_down_sync(0xffffffffu, y, o);
-            if (lane + o < 32) y += ty;
-        }
-        if (lane == 0) s_wp[warp][c] = y;
-        const R ey = __shfl_down_sync(0xffffffffu, y, 1);
-        b[c] = (lane == 31) ? R(0) : ey;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int c = 0; c < kMexNC; ++c) {
-        R p0 = s_p0[c];
-        for (int w = NW - 1; w > warp; --w) p0 += s_wp[w][c];
-        b[c] = p0 + b[c];
-    }
+    for (int c = 0; c < kMexNC; ++c) b[c] = s_p0[c] + ts[(size_t)(kMexNC + c) * kMexThreads];
     const R s1 = scale, s2 = scale * scale;
 #pragma unroll 1
     for (int k = kMexP - 1; k >= 0; --k) {
@@ -454,7 +448,7 @@ struct MexBuffers {
     Vec4<R>* sorted;
     double* tile_agg;
     double* carry;
-    R* thread_sums;      // [tile][2 * kMexNC][kMexThreads]
+    R* thread_sums;      // [tile][2 * kMexNC][kMexThreads], in-tile exclusive prefix / suffix
 };
 
 template <typename R>
