@@ -261,7 +261,7 @@ __global__ void batch_finalize_kernel(const void* __restrict__ plan,
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) {
         const int am = m < 0 ? -m : m;
-        coeffs[warp] = s * c_tab.knorm[l * (l + 1) / 2 + am] * c_tab.inv_j[n][l];
+        coeffs[warp] = s * c_tab.knorm[l * (l + 1) / 2 + am] * c_tab.inv_j[n][l] * geg_gamma(0, l, n);
     }
 }
 
@@ -293,7 +293,7 @@ batch_field_kernel(const Vec4<R>* __restrict__ posm, const void* __restrict__ pl
                 const int m = (c == 0) ? 0 : ((c & 1) ? (c + 1) / 2 : -(c / 2));
                 const int am = m < 0 ? -m : m;
                 v = (R)(coeffs[in.coef_offset + (int64_t)n * nj + l * l + l + m] *
-                        c_tab.knorm[l * (l + 1) / 2 + am]);
+                        c_tab.knorm[l * (l + 1) / 2 + am] * geg_gamma(0, l, n));
             }
             cs[e] = v;
         }

@@ -101,6 +101,15 @@ struct BasisTables {
     double ga_cb_d[kLmaxLimit + 1][kNmaxLimit + 1];
     double gb_cb_d[kLmaxLimit + 1][kNmaxLimit + 1];
     double inv_j_cb[kNmaxLimit + 1][kLmaxLimit + 1];
+    // Rescaled polynomials Ct_n = C_n / gam_n, gam_n = a_1 a_2 ... a_n
+    // (gam_0 = 1), obey Ct_n = xi Ct_{n-1} - bs_n Ct_{n-2} with
+    // bs_n = b_n / (a_n a_{n-1}) (n >= 2; bs_1 = 0), and their derivatives
+    // Dt_n = Ct_{n-1} + xi Dt_{n-1} - bs_n Dt_{n-2}: one instruction fewer
+    // per step than the plain recursion.  The kernels recur on Ct and fold
+    // gam_n into the coefficients.  [basis][l][n], basis 0 HO, 1 CB.
+    float gbs_f[2][kLmaxLimit + 1][kNmaxLimit + 1];
+    double gbs_d[2][kLmaxLimit + 1][kNmaxLimit + 1];
+    double ggam[2][kLmaxLimit + 1][kNmaxLimit + 1];
 };
 
 constexpr BasisTables make_tables() {
@@ -162,21 +171,33 @@ constexpr BasisTables make_tables() {
             t.inv_j_cb[n][l] = 1.0 / (-K * num / den);
         }
     }
+    for (int basis = 0; basis < 2; ++basis) {
+        for (int l = 0; l <= kLmaxLimit; ++l) {
+            double gam = 1.0;
+            for (int n = 0; n <= kNmaxLimit; ++n) {
+                const double a = basis == 0 ? t.ga_d[l][n] : t.ga_cb_d[l][n];
+                const double b = basis == 0 ? t.gb_d[l][n] : t.gb_cb_d[l][n];
+                const double ap = n >= 2 ? (basis == 0 ? t.ga_d[l][n - 1] : t.ga_cb_d[l][n - 1]) : 0.0;
+                if (n >= 1) gam *= a;
+                const double bs = n >= 2 ? b / (a * ap) : 0.0;
+                t.gbs_d[basis][l][n] = bs;
+                t.gbs_f[basis][l][n] = (float)bs;
+                t.ggam[basis][l][n] = gam;
+            }
+        }
+    }
     return t;
 }
 
 static __constant__ BasisTables c_tab = make_tables();
 
-// Gegenbauer recursion constants of radial basis B (0 Hernquist-Ostriker,
-// 1 Clutton-Brock)
-template <typename R, int B = 0> __device__ __forceinline__ R geg_a(int l, int n) {
-    if constexpr (sizeof(R) == 4) return B == 0 ? c_tab.ga_f[l][n] : c_tab.ga_cb_f[l][n];
-    else return B == 0 ? c_tab.ga_d[l][n] : c_tab.ga_cb_d[l][n];
+// rescaled Gegenbauer recursion constant bs_n and scale gam_n of radial basis
+// B (0 Hernquist-Ostriker, 1 Clutton-Brock; see BasisTables)
+template <typename R, int B = 0> __device__ __forceinline__ R geg_bs(int l, int n) {
+    if constexpr (sizeof(R) == 4) return c_tab.gbs_f[B][l][n];
+    else return c_tab.gbs_d[B][l][n];
 }
-template <typename R, int B = 0> __device__ __forceinline__ R geg_b(int l, int n) {
-    if constexpr (sizeof(R) == 4) return B == 0 ? c_tab.gb_f[l][n] : c_tab.gb_cb_f[l][n];
-    else return B == 0 ? c_tab.gb_d[l][n] : c_tab.gb_cb_d[l][n];
-}
+__device__ __forceinline__ double geg_gamma(int basis, int l, int n) { return c_tab.ggam[basis][l][n]; }
 __device__ __forceinline__ double inv_j_of(int basis, int n, int l) {
     return basis == 0 ? c_tab.inv_j[n][l] : c_tab.inv_j_cb[n][l];
 }

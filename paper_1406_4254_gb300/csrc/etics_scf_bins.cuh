@@ -130,7 +130,7 @@ __device__ __forceinline__ void bin_segment(R (&acc)[NR][kBinCap], const R* Ys, 
 #pragma unroll
         for (int n = 0; n < NR; ++n) {
             if (n > 0) {
-                const R cnew = geg_a<R>(g.l, n) * xi * cn - geg_b<R>(g.l, n) * cm1;
+                const R cnew = fma(xi, cn, -geg_bs<R>(g.l, n) * cm1);   // rescaled
                 cm1 = cn;
                 cn = cnew;
             }
@@ -265,7 +265,7 @@ __global__ void scf_finalize_bins_kernel(const double* __restrict__ partial, int
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) {
         const int am = m < 0 ? -m : m;
-        coeffs[warp] = s * c_tab.knorm[l * (l + 1) / 2 + am] * c_tab.inv_j[n][l];
+        coeffs[warp] = s * c_tab.knorm[l * (l + 1) / 2 + am] * c_tab.inv_j[n][l] * geg_gamma(0, l, n);
     }
 }
 

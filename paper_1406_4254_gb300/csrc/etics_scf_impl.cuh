@@ -92,9 +92,10 @@ __device__ __forceinline__ void angular_levels(R (&C)[3][LMU + 1], R (&S)[3][LMU
     }
 }
 
-// phase 1, radial part: Rs[l][n][k] = m phi_nl(r_k) / r^l = w_l C_n(xi) for
-// levels l in [l_begin, l_end] (compile-time recursion over the level, n
-// unrolled to NR so the recursion constants are immediates).  Rows n > n_max
+// phase 1, radial part: Rs[l][n][k] = m phi_nl(r_k) / (r^l gam_n) = w_l Ct_n(xi)
+// for levels l in [l_begin, l_end] (compile-time recursion over the level, n
+// unrolled to NR so the recursion constants are immediates; Ct_n the rescaled
+// Gegenbauer polynomial, gam_n restored in the finalize).  Rows n > n_max
 // stay zero.  w_l = m pre0 st^l (RadialSeed of basis B).
 template <typename R, int NR, int L, int LMU, int B = 0>
 __device__ __forceinline__ void radial_levels(R* Rs, int T, int k, int n_max, int l_begin,
@@ -108,7 +109,7 @@ __device__ __forceinline__ void radial_levels(R* Rs, int T, int k, int n_max, in
 #pragma unroll
             for (int n = 1; n < NR; ++n) {
                 if (n <= n_max) {
-                    const R cn = geg_a<R, B>(L, n) * xi * c - geg_b<R, B>(L, n) * cm1;
+                    const R cn = fma(xi, c, -geg_bs<R, B>(L, n) * cm1);
                     cm1 = c;
                     c = cn;
                     row[(size_t)n * T] = w * c;
@@ -275,7 +276,8 @@ static __global__ void scf_finalize_kernel(const double* __restrict__ partial, i
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) {
         const int am = m < 0 ? -m : m;
-        coeffs[warp] = s * c_tab.knorm[l * (l + 1) / 2 + am] * inv_j_of(basis, n, l);
+        coeffs[warp] = s * c_tab.knorm[l * (l + 1) / 2 + am] * inv_j_of(basis, n, l) *
+                       geg_gamma(basis, l, n);
     }
 }
 
@@ -315,10 +317,11 @@ struct FieldEval {
 #pragma unroll (NM1 > 0 ? NM1 : 1)
             for (int n = 0; n <= nlim; ++n, row += stride) {
                 if (n > 0) {
-                    const R a = geg_a<R, BASIS>(L, n), b = geg_b<R, BASIS>(L, n);
-                    const R cnew = a * xi * cn - b * cm1;
+                    // rescaled polynomials (the table holds gam_n c_nlm)
+                    const R bs = geg_bs<R, BASIS>(L, n);
+                    const R cnew = fma(xi, cn, -bs * cm1);
                     if (ACC) {
-                        const R dnew = a * (cn + xi * dn) - b * dm1;
+                        const R dnew = fma(-bs, dm1, fma(xi, dn, cn));
                         dm1 = dn;
                         dn = dnew;
                     }
@@ -392,7 +395,8 @@ scf_field_kernel(const Vec4<R>* __restrict__ posm, int64_t N, int n_max, int l_m
         if (c < 2 * l + 1) {
             const int m = (c == 0) ? 0 : ((c & 1) ? (c + 1) / 2 : -(c / 2));
             const int am = m < 0 ? -m : m;
-            v = (R)(coeffs[(size_t)n * nj + l * l + l + m] * c_tab.knorm[l * (l + 1) / 2 + am]);
+            v = (R)(coeffs[(size_t)n * nj + l * l + l + m] * c_tab.knorm[l * (l + 1) / 2 + am] *
+                    geg_gamma(B, l, n));
         }
         cs[e] = v;
     }
