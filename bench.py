@@ -88,6 +88,14 @@ def mex_bytes(fp64=False):
     return b + (3 * 16 if fp64 else 0)
 
 
+def fp32_peak_tflops():
+    """FP32 CUDA-core peak derived from unit counts and the maximum SM clock."""
+    return 152 * 128 * 2 * 2070.0 * 1e6 / 1e12
+
+
+MEX_L_LIMIT = 6    # compiled l_max limit of the MEX kernels (ETICS_MEX_LMAX_LIMIT)
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -857,6 +865,69 @@ def run_gemm(args):
             "max_rel_err_vs_fp32_product": err}
 
 
+def run_sweep(args):
+    """Shape sweeps of the paper's scaling study (Sec. 5: time against N,
+    l_max and n_max): SCF (coefficients + field) and MEX timed separately,
+    mixed precision, on the flattened Hernquist model of the headline
+    workload (the first N particles of one 2^24 realisation).  Each point is
+    the median of 5 calls timed with CUDA events, L2 flushed before each.
+      N in 2^14 .. 2^24 at (n_max, l_max) = (10, 6);
+      l_max in 0..10 at N = 2^20, n_max = 10 (MEX up to its compiled limit 6);
+      n_max in 0..16 at N = 2^20, l_max = 6 (SCF only).
+    fp32_frac: algorithmic flop per particle (the counts of the headline
+    kernels) x N / time, over the derived FP32 peak."""
+    import torch
+    from paper_1406_4254_gb300 import etics, inputs
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    peak = fp32_peak_tflops() * 1e12
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nmax_all = 1 << 24
+    xall = torch.tensor(inputs.hernquist(nmax_all, seed=args.seed, axes=(1.0, 0.8, 0.6)),
+                        dtype=torch.float32, device=dev)
+
+    def timed(fn, reps=5, warm=2):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1)
+            t0.record()
+            fn()
+            t1.record()
+            torch.cuda.synchronize()
+            ts.append(t0.elapsed_time(t1))
+        return statistics.median(ts)
+
+    def point(n, n_max, l_max, scf=True, mex=True):
+        x = xall[:n]
+        out = torch.empty_like(x)
+        res = {"N": n, "n_max": n_max, "l_max": l_max}
+        if scf:
+            coeffs = torch.empty((n_max + 1, (l_max + 1) ** 2), dtype=torch.float64, device=dev)
+            ws = etics.workspace(n, n_max, l_max, etics.SCF, etics.MIXED, dev)
+            ms = timed(lambda: (etics.scf_coeffs(x, n_max, l_max, out=coeffs, ws=ws),
+                                etics.scf_field(x, coeffs, n_max, l_max, out=out)))
+            flop = scf_coeff_flops(n_max, l_max) + scf_field_flops(n_max, l_max)
+            res.update(scf_ms=ms, scf_pf_per_s=n / (ms * 1e-3),
+                       scf_fp32_frac=flop * n / (ms * 1e-3) / peak)
+        if mex and l_max <= MEX_L_LIMIT:
+            ws = etics.workspace(n, 0, l_max, etics.MEX, etics.MIXED, dev)
+            ms = timed(lambda: etics.mex_field(x, l_max, out=out, ws=ws))
+            res.update(mex_ms=ms, mex_pf_per_s=n / (ms * 1e-3),
+                       mex_fp32_frac=mex_flops(l_max) * n / (ms * 1e-3) / peak)
+        return res
+
+    sweep_n = [point(1 << k, N_MAX, L_MAX) for k in range(14, 25)]
+    sweep_l = [point(1 << 20, N_MAX, l) for l in range(0, 11)]
+    sweep_nmax = [point(1 << 20, nm, L_MAX, mex=False) for nm in range(0, 17)]
+    etics.check_error()
+    return {"experiment": "sweep", "workload": "hernquist-1:0.8:0.6, first N of a 2^24 "
+            "realisation, mixed precision", "fp32_peak_tflops": peak * 1e-12,
+            "fp32_peak_note": FP32_PEAK_NOTE, "N": sweep_n, "l_max": sweep_l, "n_max": sweep_nmax}
+
+
 def emit(obj):
     print(json.dumps(obj), flush=True)
 
@@ -872,7 +943,8 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=65536)
-    ap.add_argument("--experiment", choices=["leapfrog", "batch", "surrogate", "accuracy", "gemm"],
+    ap.add_argument("--experiment", choices=["leapfrog", "batch", "surrogate", "accuracy", "gemm",
+                                             "sweep"],
                     default=None)
     ap.add_argument("--gemm-mnk", type=int, nargs=3, default=[16384, 4096, 4096])
     ap.add_argument("--acc-n", type=int, nargs="+", default=[1000, 10000, 100000, 1000000])
@@ -896,6 +968,9 @@ def main():
         return
     if args.experiment == "batch":
         emit(run_batch(args))
+        return
+    if args.experiment == "sweep":
+        emit(run_sweep(args))
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -934,8 +1009,7 @@ def main():
     st = res["stage"]
     # every timed kernel against the roofline that bounds it; the dominant one
     # (largest share of the step) is the headline roofline
-    sm_max = 2070.0
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12       # TFLOP/s
+    fp32_peak = fp32_peak_tflops()
     traffic = kernel_traffic()
     kern = {
         "scf_coeff_kernel": ("alu", st["coef_kernel"], scf_coeff_flops(N_MAX, L_MAX)),

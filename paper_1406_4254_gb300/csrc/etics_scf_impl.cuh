@@ -314,7 +314,7 @@ struct FieldEval {
             const int stride = NM1 > 0 ? kStride : ncols;
             const int nlim = NM1 > 0 ? NM1 - 1 : n_max;
             const R* row = cs + CO;
-#pragma unroll (NM1 > 0 ? NM1 : 1)
+#pragma unroll (NM1 > 0 ? NM1 : 4)
             for (int n = 0; n <= nlim; ++n, row += stride) {
                 if (n > 0) {
                     // rescaled polynomials (the table holds gam_n c_nlm)
