@@ -870,7 +870,8 @@ def run_sweep(args):
     l_max and n_max): SCF (coefficients + field) and MEX timed separately,
     mixed precision, on the flattened Hernquist model of the headline
     workload (the first N particles of one 2^24 realisation).  Each point is
-    the median of 5 calls timed with CUDA events, L2 flushed before each.
+    the median of 5 calls timed with CUDA events, L2 flushed before each; the
+    SCF coefficient and field passes are also timed on their own.
       N in 2^14 .. 2^24 at (n_max, l_max) = (10, 6);
       l_max in 0..10 at N = 2^20, n_max = 10 (MEX up to its compiled limit 6);
       n_max in 0..16 at N = 2^20, l_max = 6 (SCF only).
@@ -909,9 +910,12 @@ def run_sweep(args):
             ws = etics.workspace(n, n_max, l_max, etics.SCF, etics.MIXED, dev)
             ms = timed(lambda: (etics.scf_coeffs(x, n_max, l_max, out=coeffs, ws=ws),
                                 etics.scf_field(x, coeffs, n_max, l_max, out=out)))
+            mc = timed(lambda: etics.scf_coeffs(x, n_max, l_max, out=coeffs, ws=ws))
+            mf = timed(lambda: etics.scf_field(x, coeffs, n_max, l_max, out=out))
             flop = scf_coeff_flops(n_max, l_max) + scf_field_flops(n_max, l_max)
             res.update(scf_ms=ms, scf_pf_per_s=n / (ms * 1e-3),
-                       scf_fp32_frac=flop * n / (ms * 1e-3) / peak)
+                       scf_fp32_frac=flop * n / (ms * 1e-3) / peak,
+                       scf_coeff_ms=mc, scf_field_ms=mf)
         if mex and l_max <= MEX_L_LIMIT:
             ws = etics.workspace(n, 0, l_max, etics.MEX, etics.MIXED, dev)
             ms = timed(lambda: etics.mex_field(x, l_max, out=out, ws=ws))
