@@ -8,6 +8,10 @@ namespace etics {
 
 // ---- SCF (etics_scf_f32.cu / etics_scf_f64.cu) ----------------------------
 size_t scf_workspace_f32(int64_t N, int n_max, int l_max, int num_sms);
+// per-warp-bin coefficient pass at (14, 8) (etics_scf_bins_f32.cu)
+size_t scf_bins148_workspace_f32(int num_sms);
+int scf_coeffs_bins148_f32(const void* posm, int64_t N, double* coeffs, void* ws,
+                           const LaunchCtx& ctx);
 size_t scf_workspace_f64(int64_t N, int n_max, int l_max, int num_sms);
 int scf_coeffs_f32(const void* posm, int64_t N, int n_max, int l_max, double* coeffs, void* ws,
                    const LaunchCtx& ctx);

@@ -160,11 +160,19 @@ __device__ __forceinline__ void bin_dispatch(int warp, R (&acc)[NR][kBinCap], co
     }
 }
 
-template <typename R, int NR, int LM>
-__global__ void __launch_bounds__(BinConst<LM>::nbins * 32, 2)
+// TP: particles per tile (at most one per thread in phase 1; the default,
+// one per thread, keeps every thread busy there; fewer particles per tile
+// keep the two basis buffers of a large l_max within shared memory).
+// MINB: resident blocks per SM the registers are sized for.
+template <int LM>
+constexpr int bins_threads() { return BinConst<LM>::nbins * 32; }
+template <typename R, int NR, int LM, int TP = bins_threads<LM>(), int MINB = 2>
+__global__ void __launch_bounds__(bins_threads<LM>(), MINB)
 scf_coeff_bins_kernel(ScfBinParams p) {
     constexpr int NB = BinConst<LM>::nbins;
-    constexpr int T = NB * 32;          // particles per tile: one per thread in phase 1
+    constexpr int TH = NB * 32;         // threads: one warp per bin
+    constexpr int T = TP;               // particles per tile
+    static_assert(T <= TH && T % 32 == 0, "tile");
     constexpr int NCOL = (LM + 1) * (LM + 1);
     constexpr int NOUT = NB * NR * kBinCap;
     using V4 = Vec4<R>;
@@ -179,7 +187,7 @@ scf_coeff_bins_kernel(ScfBinParams p) {
     R* Ys1 = reinterpret_cast<R*>(s_rad1 + T);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const V4* posm = reinterpret_cast<const V4*>(p.posm);
-    for (int e = tid; e < NOUT; e += T) accd[e] = 0.0;
+    for (int e = tid; e < NOUT; e += TH) accd[e] = 0.0;
     R acc[NR][kBinCap];
 #pragma unroll
     for (int n = 0; n < NR; ++n)
@@ -201,10 +209,13 @@ scf_coeff_bins_kernel(ScfBinParams p) {
     };
     auto load = [&](int tile) -> V4 {
         const int64_t gi = (int64_t)tile * T + tid;
-        return (tile < p.ntiles && gi < p.N) ? ld4(posm + gi) : mk4<R>(R(0), R(0), R(0), R(0));
+        return (tid < T && tile < p.ntiles && gi < p.N) ? ld4(posm + gi)
+                                                      : mk4<R>(R(0), R(0), R(0), R(0));
     };
-    // phase 1: one particle per thread -> angular basis + radial seeds
+    // phase 1: one particle per thread (threads tid < T) -> angular basis +
+    // radial seeds
     auto basis = [&](const V4& cur, V4* s_rad, R* Ys) {
+        if (T < TH && tid >= T) return;
         R x = R(0), y = R(0), z = R(0), m = R(0);
         if (finite4(cur.x, cur.y, cur.z, cur.w)) { x = cur.x; y = cur.y; z = cur.z; m = cur.w; }
         else report(p.err, ETICS_ERR_NONFINITE);
@@ -239,7 +250,7 @@ scf_coeff_bins_kernel(ScfBinParams p) {
     if (since) flush();
     __syncthreads();
     double* out = p.partial + (size_t)blockIdx.x * NOUT;
-    for (int e = tid; e < NOUT; e += T) out[e] = accd[e];
+    for (int e = tid; e < NOUT; e += TH) out[e] = accd[e];
 }
 
 // sum block partials in a fixed order; one warp per output c[n][l*l+l+m]
@@ -269,30 +280,32 @@ __global__ void scf_finalize_bins_kernel(const double* __restrict__ partial, int
     }
 }
 
-template <typename R, int NR, int LM>
+template <typename R, int NR, int LM, int MINB = 2>
 inline size_t scf_bins_workspace(int num_sms) {
-    return (size_t)2 * num_sms * BinConst<LM>::nbins * NR * kBinCap * sizeof(double);
+    return (size_t)MINB * num_sms * BinConst<LM>::nbins * NR * kBinCap * sizeof(double);
 }
 
-template <typename R, int NR, int LM>
+template <typename R, int NR, int LM, int TP = bins_threads<LM>(), int MINB = 2>
 inline int scf_coeffs_bins_launch(const void* posm, int64_t N, double* coeffs, void* ws,
                                   const LaunchCtx& ctx) {
     constexpr int NB = BinConst<LM>::nbins;
-    constexpr int T = NB * 32;
+    constexpr int TH = NB * 32;
+    constexpr int T = TP;
     const int ntiles = (int)((N + T - 1) / T);
-    int grid = ctx.num_sms * 2;
+    int grid = ctx.num_sms * MINB;
     if (grid > ntiles) grid = ntiles > 0 ? ntiles : 1;
     ScfBinParams p{posm, N, ntiles, reinterpret_cast<double*>(ws), ctx.err};
     constexpr int NOUT = NB * NR * kBinCap;
     constexpr size_t smem = ((NOUT * sizeof(double) + 15) / 16) * 16 +
                             2 * (T * sizeof(Vec4<R>) + (size_t)(LM + 1) * (LM + 1) * T * sizeof(R));
+    static_assert(smem <= 227 * 1024, "bins kernel shared memory");
     int nblocks = 0;
     if (ntiles > 0) {
-        auto k = scf_coeff_bins_kernel<R, NR, LM>;
+        auto k = scf_coeff_bins_kernel<R, NR, LM, TP, MINB>;
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ||
             cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100))
             return ETICS_ERR_CUDA;
-        k<<<grid, T, smem, ctx.stream>>>(p);
+        k<<<grid, TH, smem, ctx.stream>>>(p);
         if (cudaGetLastError() != cudaSuccess) return ETICS_ERR_CUDA;
         ++*ctx.launches;
         nblocks = grid;

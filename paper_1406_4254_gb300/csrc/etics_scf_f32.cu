@@ -8,13 +8,15 @@ size_t scf_workspace_f32(int64_t N, int n_max, int l_max, int num_sms) {
     size_t a = scf_workspace<float>(N, n_max, l_max, num_sms);
     size_t b = 0;
     if (n_max == 10 && l_max == 6) b = scf_bins_workspace<float, 11, 6>(num_sms);
+    if (n_max == 14 && l_max == 8) b = scf_bins148_workspace_f32(num_sms);
     return a > b ? a : b;
 }
 int scf_coeffs_f32(const void* posm, int64_t N, int n_max, int l_max, double* coeffs, void* ws,
                    const LaunchCtx& ctx) {
-    // specialised per-warp-bin kernel for the paper's standard (10, 6) expansion
+    // specialised per-warp-bin kernels for the paper's (10, 6) and (14, 8) expansions
     if (n_max == 10 && l_max == 6)
         return scf_coeffs_bins_launch<float, 11, 6>(posm, N, coeffs, ws, ctx);
+    if (n_max == 14 && l_max == 8) return scf_coeffs_bins148_f32(posm, N, coeffs, ws, ctx);
     return scf_coeffs_launch<float>(posm, N, n_max, l_max, coeffs, ws, ctx);
 }
 int scf_field_f32(const void* posm, int64_t N, int n_max, int l_max, const double* coeffs,
