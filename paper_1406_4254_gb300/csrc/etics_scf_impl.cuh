@@ -309,6 +309,13 @@ struct FieldEval {
             R A[NC], B[NC];
 #pragma unroll
             for (int c = 0; c < NC; ++c) { A[c] = R(0); B[c] = R(0); }
+            // FP32: the column sums run as packed pairs (columns 2i, 2i+1:
+            // one paired FMA for two columns; the padded table has a zero
+            // partner for the last, odd column)
+            constexpr int NP = (NC + 1) / 2;
+            float2 A2[NP], B2[NP];
+#pragma unroll
+            for (int i = 0; i < NP; ++i) { A2[i] = make_float2(0.f, 0.f); B2[i] = make_float2(0.f, 0.f); }
             R cm1 = R(0), cn = R(1), dm1 = R(0), dn = R(0);
             constexpr int kStride = NM1 > 0 ? col_offset_c(LM + 1) : 0;
             const int stride = NM1 > 0 ? kStride : ncols;
@@ -328,18 +335,41 @@ struct FieldEval {
                     cm1 = cn;
                     cn = cnew;
                 }
+                if constexpr (sizeof(R) == 4) {
+                    const float2 cc = make_float2(cn, cn), dd = make_float2(dn, dn);
 #pragma unroll
-                for (int q = 0; q < NQ; ++q) {
-                    const V4 v = ld4(reinterpret_cast<const V4*>(row) + q);
-                    const R vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int c = 4 * q + e;
-                        if (c < NC) {
-                            A[c] = fma(vv[e], cn, A[c]);
-                            if (ACC) B[c] = fma(vv[e], dn, B[c]);
+                    for (int q = 0; q < NQ; ++q) {
+                        const V4 v = ld4(reinterpret_cast<const V4*>(row) + q);
+                        if (2 * q < NP) {
+                            A2[2 * q] = __ffma2_rn(make_float2(v.x, v.y), cc, A2[2 * q]);
+                            if (ACC) B2[2 * q] = __ffma2_rn(make_float2(v.x, v.y), dd, B2[2 * q]);
+                        }
+                        if (2 * q + 1 < NP) {
+                            A2[2 * q + 1] = __ffma2_rn(make_float2(v.z, v.w), cc, A2[2 * q + 1]);
+                            if (ACC) B2[2 * q + 1] = __ffma2_rn(make_float2(v.z, v.w), dd, B2[2 * q + 1]);
                         }
                     }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < NQ; ++q) {
+                        const V4 v = ld4(reinterpret_cast<const V4*>(row) + q);
+                        const R vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int c = 4 * q + e;
+                            if (c < NC) {
+                                A[c] = fma(vv[e], cn, A[c]);
+                                if (ACC) B[c] = fma(vv[e], dn, B[c]);
+                            }
+                        }
+                    }
+                }
+            }
+            if constexpr (sizeof(R) == 4) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    A[c] = (c & 1) ? A2[c / 2].y : A2[c / 2].x;
+                    B[c] = (c & 1) ? B2[c / 2].y : B2[c / 2].x;
                 }
             }
             // angular sums with the level's harmonics
