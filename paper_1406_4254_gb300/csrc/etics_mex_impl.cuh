@@ -234,7 +234,8 @@ __device__ __forceinline__ void scan_rows(R (&v)[kMexNC], R* buf, R* total, int 
 // pass 1: gather into radial order + per-tile FP64 moment sums
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void __launch_bounds__(kMexThreads, 4)   // 4 blocks/SM: 16 warps hide the gather latency
+// FP32: 4 blocks/SM (16 warps hide the gather latency); FP64 needs the registers
+__global__ void __launch_bounds__(kMexThreads, sizeof(R) == 4 ? 4 : 1)
 mex_pass1_kernel(const Vec4<R>* __restrict__ posm, const uint32_t* __restrict__ perm, int64_t N,
                  int l_max, Vec4<R>* __restrict__ sorted, double* __restrict__ tile_agg,
                  R* __restrict__ thread_sums, unsigned* err) {
