@@ -26,7 +26,6 @@ constexpr uint32_t kCountMask = (1u << 30) - 1;
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagInc = 2u << 30;
 constexpr int kSpinLimit = 1 << 22;
-constexpr int kMaxTieRun = 256;
 
 int sort_tiles(int64_t N) { return (int)((N + kSortTile - 1) / kSortTile); }
 
@@ -362,8 +361,9 @@ onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
 
 // Runs of equal high words: order by (low word of the FP64 r^2, index).  The
 // run's first element owns it; the low words are evaluated here, in FP64, for
-// the run members only.  Runs longer than kMaxTieRun are reported as
-// unsupported (left in index order).
+// the run members only.  The radix passes are stable and began from index
+// order, so a run's members arrive in index order: a stable sort by the low
+// word alone gives the (low word, index) order.
 template <typename R>
 __device__ __forceinline__ uint32_t r2_low(const Vec4<R>* posm, uint32_t i) {
     const Vec4<R> v = ld4(posm + i);
@@ -371,62 +371,132 @@ __device__ __forceinline__ uint32_t r2_low(const Vec4<R>* posm, uint32_t i) {
     return (uint32_t)(uint64_t)__double_as_longlong(r2_fp64((double)v.x, (double)v.y, (double)v.z));
 }
 
-constexpr int kFixThreads = 256;
+constexpr int kFixThreads = 256;   // one thread per digit in the block sort below
 constexpr int kFixTile = 2048;
-constexpr int kFixLocal = 16;   // runs up to this length are sorted in registers/L1
+constexpr int kFixLocal = 16;      // runs up to this length: one thread, in registers
+constexpr int kFixLongMax = kFixTile / (kFixLocal + 1) + 1;   // long runs starting in a tile
 
+// a run of at most kFixLocal members, by one thread (insertion sort)
 template <typename R>
-__device__ __forceinline__ void sort_run(const Vec4<R>* posm, uint32_t* val, int64_t s, int64_t e) {
-    const int len = (int)(e - s + 1);
-    if (len <= kFixLocal) {
-        uint32_t lows[kFixLocal], ids[kFixLocal];
-        for (int a = 0; a < len; ++a) ids[a] = val[s + a];
-        for (int a = 0; a < len; ++a) lows[a] = r2_low<R>(posm, ids[a]);
-        for (int a = 1; a < len; ++a) {
-            const uint32_t va = ids[a], la = lows[a];
-            int b = a - 1;
-            while (b >= 0 && (lows[b] > la || (lows[b] == la && ids[b] > va))) {
-                ids[b + 1] = ids[b];
-                lows[b + 1] = lows[b];
-                --b;
-            }
-            ids[b + 1] = va;
-            lows[b + 1] = la;
+__device__ __forceinline__ void sort_run_local(const Vec4<R>* posm, uint32_t* val, int64_t s,
+                                               int len) {
+    uint32_t lows[kFixLocal], ids[kFixLocal];
+    for (int a = 0; a < len; ++a) ids[a] = val[s + a];
+    for (int a = 0; a < len; ++a) lows[a] = r2_low<R>(posm, ids[a]);
+    for (int a = 1; a < len; ++a) {
+        const uint32_t va = ids[a], la = lows[a];
+        int b = a - 1;
+        while (b >= 0 && (lows[b] > la || (lows[b] == la && ids[b] > va))) {
+            ids[b + 1] = ids[b];
+            lows[b + 1] = lows[b];
+            --b;
         }
-        for (int a = 0; a < len; ++a) val[s + a] = ids[a];
-    } else {
-        // longer runs (rare): insertion sort in place, low words recomputed
-        for (int64_t a = s + 1; a <= e; ++a) {
-            const uint32_t va = val[a], la = r2_low<R>(posm, va);
-            int64_t b = a - 1;
-            while (b >= s) {
-                const uint32_t vb = val[b], lb = r2_low<R>(posm, vb);
-                if (lb < la || (lb == la && vb < va)) break;
-                val[b + 1] = vb;
-                --b;
+        ids[b + 1] = va;
+        lows[b + 1] = la;
+    }
+    for (int a = 0; a < len; ++a) val[s + a] = ids[a];
+}
+
+// A long run (any length), by the whole block: a stable LSD radix sort of
+// the members by their low word, 4 passes of 8 bits, ping-ponging between
+// val (the sorted order) and tmp (the sort's spare value buffer, over the
+// same positions); the low word is re-evaluated from the particle whenever it
+// is needed, so nothing is written outside val/tmp[s, s + len).  Each pass:
+// digit histogram, exclusive scan, then chunks of kFixThreads members in
+// order, each member ranked among equal digits of its warp (ballots) and of
+// the earlier warps of the chunk.
+template <typename R>
+__device__ void sort_run_block(const Vec4<R>* posm, uint32_t* val, uint32_t* tmp, int64_t s,
+                               int64_t len, uint32_t (*s_cnt)[256], uint32_t* s_off,
+                               uint32_t* s_wsum) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = kFixThreads / 32;
+    for (int pass = 0; pass < 4; ++pass) {
+        const int shift = 8 * pass;
+        const uint32_t* src = (pass & 1) ? tmp : val;
+        uint32_t* dst = (pass & 1) ? val : tmp;
+        for (int w = 0; w < NW; ++w) s_cnt[w][tid] = 0u;
+        __syncthreads();
+        for (int64_t i = tid; i < len; i += kFixThreads)
+            atomicAdd(&s_cnt[0][(r2_low<R>(posm, src[s + i]) >> shift) & 255u], 1u);
+        __syncthreads();
+        {
+            // exclusive scan over the 256 digits (thread = digit)
+            const uint32_t c = s_cnt[0][tid];
+            uint32_t x = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += t;
             }
-            val[b + 1] = va;
+            if (lane == 31) s_wsum[warp] = x;
+            __syncthreads();
+            uint32_t b = 0;
+            for (int w = 0; w < warp; ++w) b += s_wsum[w];
+            s_off[tid] = b + x - c;
+            s_cnt[0][tid] = 0u;
+        }
+        __syncthreads();
+        for (int64_t c0 = 0; c0 < len; c0 += kFixThreads) {
+            const int64_t i = c0 + tid;
+            const bool valid = i < len;
+            const uint32_t v = valid ? src[s + i] : 0u;
+            const uint32_t d = valid ? (r2_low<R>(posm, v) >> shift) & 255u : 256u;
+            const unsigned vb = __ballot_sync(0xffffffffu, valid);
+            unsigned mask = valid ? vb : ~vb;
+#pragma unroll
+            for (int bit = 0; bit < 8; ++bit) {
+                const bool on = (d >> bit) & 1u;
+                const unsigned bal = __ballot_sync(0xffffffffu, on);
+                mask &= on ? bal : ~bal;
+            }
+            const unsigned lower = mask & ((1u << lane) - 1u);
+            if (valid && lower == 0u) s_cnt[warp][d] = (uint32_t)__popc(mask);
+            __syncthreads();
+            uint32_t total = 0;   // thread = digit: exclusive prefix over the warps
+            for (int w = 0; w < NW; ++w) {
+                const uint32_t t = s_cnt[w][tid];
+                s_cnt[w][tid] = total;
+                total += t;
+            }
+            __syncthreads();
+            if (valid) dst[s + s_off[d] + s_cnt[warp][d] + (uint32_t)__popc(lower)] = v;
+            __syncthreads();
+            s_off[tid] += total;
+            for (int w = 0; w < NW; ++w) s_cnt[w][tid] = 0u;
+            __syncthreads();
         }
     }
+    // 4 passes: the result is back in val
 }
 
 // One block per tile of kFixTile sorted positions; the keys of the tile and
 // one position on either side are staged in shared memory.  A run belongs to
-// the tile where it starts.  The block first lists the runs that start in its
-// tile, then sorts them one per thread (so the dependent loads of all runs are
-// in flight together); a run is walked in shared memory and, past the tile
-// end, in global memory.
+// the tile where it starts.  The block lists the runs that start in its tile;
+// each thread finds the end of its runs by a search over the sorted keys and
+// sorts those of at most kFixLocal members itself (so the dependent loads of
+// all short runs are in flight together); then the block sorts the longer
+// runs one after the other.  A long run may extend over later tiles: no
+// other run starts inside it, so no other block touches its positions.
 template <typename R>
 __global__ void __launch_bounds__(kFixThreads)
 tie_fixup_kernel(const uint32_t* __restrict__ key, const Vec4<R>* __restrict__ posm,
-                 uint32_t* __restrict__ val, int64_t N, unsigned* err) {
+                 uint32_t* __restrict__ val, uint32_t* __restrict__ tmp, int64_t N) {
     __shared__ uint32_t s_key[kFixTile + 2];
     __shared__ int s_runs[kFixTile / 2];
-    __shared__ int s_nruns;
+    __shared__ int s_nruns, s_nlong;
+    __shared__ int64_t s_long_s[kFixLongMax], s_long_n[kFixLongMax];
+    // the long-run sort's counters reuse the staged keys and the run list
+    // (both dead by then)
+    static_assert(sizeof(uint32_t) * (kFixThreads / 32) * 256 <= sizeof(s_key), "counters");
+    static_assert(sizeof(uint32_t) * (256 + kFixThreads / 32) <= sizeof(s_runs), "offsets");
+    auto s_cnt = reinterpret_cast<uint32_t (*)[256]>(s_key);
+    uint32_t* s_off = reinterpret_cast<uint32_t*>(s_runs);
+    uint32_t* s_wsum = s_off + 256;
     const int64_t base = (int64_t)blockIdx.x * kFixTile;
     const int64_t rem = N - base;
     const int nt = (int)(rem < kFixTile ? rem : kFixTile);
-    if (threadIdx.x == 0) s_nruns = 0;
+    if (threadIdx.x == 0) { s_nruns = 0; s_nlong = 0; }
     pdl_wait();
     // s_key[i + 1] = key[base + i] for i in [-1, nt]; sentinels outside [0, N)
     for (int i = threadIdx.x - 1; i <= nt; i += kFixThreads) {
@@ -445,17 +515,35 @@ tie_fixup_kernel(const uint32_t* __restrict__ key, const Vec4<R>* __restrict__ p
     __syncthreads();
     const int nruns = s_nruns;   // at most kFixTile / 2 (each run has >= 2 members)
     for (int r = threadIdx.x; r < nruns; r += kFixThreads) {
-        const int i = s_runs[r];
-        const uint32_t k = s_key[i + 1];
-        int li = i + 1;
-        while (li + 1 < nt && s_key[li + 2] == k) ++li;
-        int64_t j = base + li;                               // last member so far
-        if (li + 1 >= nt) {                                  // may continue past the tile
-            while (j + 1 < N && key[j + 1] == k && j - (base + i) < kMaxTieRun) ++j;
+        const int64_t s = base + s_runs[r];
+        const uint32_t k = s_key[s_runs[r] + 1];
+        // last member: the keys are sorted, so search for the last position
+        // holding k (doubling steps, then bisection; key[s + 1] == k)
+        int64_t lo = s + 1, hi = N, step = 1;
+        for (;;) {
+            const int64_t probe = lo + step;
+            if (probe >= N || key[probe] != k) { hi = probe < N ? probe : N; break; }
+            lo = probe;
+            step <<= 1;
         }
-        if (j - (base + i) >= kMaxTieRun) { report(err, ETICS_ERR_UNSUPPORTED); continue; }
-        sort_run<R>(posm, val, base + i, j);
+        while (hi - lo > 1) {
+            const int64_t mid = lo + (hi - lo) / 2;
+            if (key[mid] == k) lo = mid;
+            else hi = mid;
+        }
+        const int64_t len = lo - s + 1;
+        if (len <= kFixLocal) {
+            sort_run_local<R>(posm, val, s, (int)len);
+        } else {
+            const int slot = atomicAdd(&s_nlong, 1);   // < kFixLongMax: members do not overlap
+            s_long_s[slot] = s;
+            s_long_n[slot] = len;
+        }
     }
+    __syncthreads();   // s_key and s_runs are dead from here
+    const int nlong = s_nlong;
+    for (int r = 0; r < nlong; ++r)
+        sort_run_block<R>(posm, val, tmp, s_long_s[r], s_long_n[r], s_cnt, s_off, s_wsum);
 }
 
 // ---------------------------------------------------------------------------
@@ -514,7 +602,8 @@ int radial_sort_impl(const void* posm, int64_t N, const SortBuffers& b, const La
     // after 4 passes the sorted keys/values are back in keys_a / vals_a
     const int fg = (int)((N + kFixTile - 1) / kFixTile);
     if (launch_pdl(tie_fixup_kernel<R>, dim3(fg), dim3(kFixThreads), 0, ctx.stream,
-                   (const uint32_t*)b.keys_a, reinterpret_cast<const Vec4<R>*>(posm), b.vals_a, N, ctx.err))
+                   (const uint32_t*)b.keys_a, reinterpret_cast<const Vec4<R>*>(posm), b.vals_a,
+                   b.vals_b, N))
         return ETICS_ERR_CUDA;
     ++*ctx.launches;
     return ETICS_OK;

@@ -75,6 +75,63 @@ def test_radial_keys_are_fp64_bits(precision):
         assert bad.size == 0, (bad[:5], got[bad[:5]], ref[bad[:5]])
 
 
+def long_tie_particles(n_shell, n_copies, n_background, seed):
+    """Degenerate radial orders: a thin shell (unit vectors, r^2 within a few
+    ulps of 1: every member shares one of two sort keys, so each half is one
+    run of equal keys), copies of one point (identical r^2: a run ordered by
+    index alone), runs of 17..300 members whose r^2 differ in the low bits
+    only, inside a Hernquist background; rows shuffled."""
+    rng = np.random.default_rng(seed)
+    u = rng.normal(size=(n_shell, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    parts = [np.hstack([u, np.full((n_shell, 1), 1.0 / max(n_shell, 1))])]
+    parts.append(np.tile([0.3, -0.4, 0.5, 1e-3], (n_copies, 1)))
+    for m in (17, 18, 33, 100, 300):
+        p0 = rng.normal(size=3) * 0.7
+        k = np.arange(m)[:, None]
+        parts.append(np.hstack([p0[None, :] * (1.0 + k * 1e-12), np.full((m, 1), 1e-4)]))
+    parts.append(hernquist(n_background, seed=seed))
+    pm = np.vstack(parts)
+    return pm[rng.permutation(len(pm))]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_radial_order_long_runs(precision):
+    """Runs of equal sort keys of any length (two shell halves of ~20000, a
+    run of 3000 identical points, runs of 17..300): the order is still the
+    exact (FP64 r^2, index) order, bit for bit."""
+    pm = long_tie_particles(40000, 3000, 60000, seed=31)
+    got = etics.radial_order(device_particles(pm, precision)).cpu().numpy()
+    etics.check_error()
+    assert np.array_equal(got, oracle_order(rounded(pm, precision)))
+    # every particle at the same point: one run holding all of them
+    same = np.tile([0.25, 0.5, -1.0, 1.0], (5000, 1))
+    got = etics.radial_order(device_particles(same, precision)).cpu().numpy()
+    etics.check_error()
+    assert np.array_equal(got, np.arange(5000))
+
+
+def test_radial_order_full_shell():
+    """2^20 particles on the unit sphere (FP32): two runs of ~2^19 equal keys,
+    each ordered by one block."""
+    pm = long_tie_particles(1 << 20, 0, 0, seed=32)
+    got = etics.radial_order(device_particles(pm, "mixed")).cpu().numpy()
+    etics.check_error()
+    assert np.array_equal(got, oracle_order(rounded(pm, "mixed")))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_field_with_long_runs(precision):
+    """The MEX field of the degenerate set above against the oracle (the
+    shell's members are summed in the tie order, the same on both sides)."""
+    pm = long_tie_particles(3000, 500, 4000, seed=33)
+    ref_in = rounded(pm, precision)
+    acc_ref, pot_ref, _ = oracle.mex_field(ref_in[:, :3], ref_in[:, 3], 6)
+    out = etics.mex_field(device_particles(pm, precision), 6)
+    etics.check_error()
+    assert_field_close(out.cpu().numpy(), acc_ref, pot_ref, precision, "mex long runs")
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_radial_order_near_boundaries(precision):
     pm = near_boundary_particles(50000, 2)
