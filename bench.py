@@ -93,7 +93,7 @@ def fp32_peak_tflops():
     return 152 * 128 * 2 * 2070.0 * 1e6 / 1e12
 
 
-MEX_L_LIMIT = 6    # compiled l_max limit of the MEX kernels (ETICS_MEX_LMAX_LIMIT)
+MEX_L_LIMIT = 10   # compiled l_max limit of the MEX kernels (ETICS_MEX_LMAX_LIMIT)
 
 
 def load_peaks():
@@ -753,11 +753,12 @@ def run_accuracy(args):
     their polynomial potential recomputed from the 1-D index-symbol
     integrals, and the closed-form Hernquist and Plummer spheres.  N from
     10^3 to 10^6; realisations are stacked up to 10^6 particles per point (at
-    most 100).  MEX at l_max = 0, 2, 4, 6; SCF at l_max = 6 with n_max =
-    0..14 and at l_max = 10 with n_max = 6, 10, 14 (the paper's Fig. 8 sweep,
-    where SCF approaches MEX as n_max grows), and SCF in the Clutton-Brock
-    basis (Plummer zeroth term) at l_max = 6.  The overlap of the log10(eps)
-    histograms of SCF and MEX at l_max = 6 measures that approach."""
+    most 100).  MEX at even l_max = 0..10 (the paper's Figs. 4 and 5); SCF at
+    l_max = 6 with n_max = 0..14 and at l_max = 10 with n_max = 6, 10, 14
+    (the paper's Fig. 8 sweep, where SCF approaches MEX as n_max grows), and
+    SCF in the Clutton-Brock basis (Plummer zeroth term) at l_max = 6.  The
+    overlap of the log10(eps) histograms of SCF and MEX at the same l_max (6
+    and 10) measures that approach."""
     import torch
     from paper_1406_4254_gb300 import etics, inputs, models
     dev = torch.device("cuda", 0)
@@ -777,7 +778,7 @@ def run_accuracy(args):
             acc, _ = models.plummer_force(pm[:, :3])
         return pm, acc
 
-    methods = ([("mex", 0, l) for l in (0, 2, 4, 6)] +
+    methods = ([("mex", 0, l) for l in (0, 2, 4, 6, 8, 10)] +
                [("scf", n, 6) for n in (0, 2, 4, 6, 10, 14)] +
                [("scf", n, 10) for n in (6, 10, 14)] +
                [("scfcb", n, 6) for n in (0, 2, 6, 10)])
@@ -811,8 +812,10 @@ def run_accuracy(args):
                             "p90": float(np.quantile(e, 0.9))}
                 h, _ = np.histogram(np.log10(np.maximum(e, 1e-12)), bins=bins)
                 hist[key] = h / max(1, h.sum())
-            row["overlap_with_mex_l6"] = {k: float(np.minimum(hist[k], hist["mex_l6"]).sum())
-                                          for k in hist if k.startswith("scf_") and k.endswith("_l6")}
+            for lm in (6, 10):
+                row[f"overlap_with_mex_l{lm}"] = {
+                    k: float(np.minimum(hist[k], hist[f"mex_l{lm}"]).sum())
+                    for k in hist if k.startswith("scf_") and k.endswith(f"_l{lm}")}
             row["realisations"] = reps
             out[model][str(n)] = row
     return {"experiment": "accuracy", "precision": "FP64",

@@ -67,7 +67,7 @@ enum etics_out { ETICS_OUT_ACC = 1, ETICS_OUT_POT = 2 };   /* force/potential/bo
 
 #define ETICS_NMAX_LIMIT 16
 #define ETICS_LMAX_LIMIT 14
-#define ETICS_MEX_LMAX_LIMIT 6
+#define ETICS_MEX_LMAX_LIMIT 10
 
 /* Bytes of device workspace a call of `method` (ETICS_SCF: etics_scf_coeffs
  * and etics_leapfrog_step with SCF; ETICS_MEX: etics_mex_field,

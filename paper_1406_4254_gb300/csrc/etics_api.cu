@@ -83,7 +83,8 @@ size_t etics_workspace_bytes(int64_t N, int n_max, int l_max, int method, int pr
     }
     if (method == ETICS_MEX) {
         if (l_max > ETICS_MEX_LMAX_LIMIT) return 0;
-        return precision == ETICS_MIXED ? etics::mex_workspace_f32(N) : etics::mex_workspace_f64(N);
+        return precision == ETICS_MIXED ? etics::mex_workspace_f32(N, l_max)
+                                        : etics::mex_workspace_f64(N, l_max);
     }
     return 0;
 }

@@ -50,8 +50,8 @@ template <typename R>
 int radial_sort_impl(const void* posm, int64_t N, const SortBuffers& b, const LaunchCtx& ctx);
 
 // ---- MEX (etics_mex_f32.cu / etics_mex_f64.cu) ----------------------------
-size_t mex_workspace_f32(int64_t N);
-size_t mex_workspace_f64(int64_t N);
+size_t mex_workspace_f32(int64_t N, int l_max);
+size_t mex_workspace_f64(int64_t N, int l_max);
 int mex_field_f32(const void* posm, int64_t N, int l_max, void* out, int out_mask, void* ws,
                   const LaunchCtx& ctx);
 int mex_field_f64(const void* posm, int64_t N, int l_max, void* out, int out_mask, void* ws,

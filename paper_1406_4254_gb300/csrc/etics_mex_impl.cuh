@@ -32,8 +32,29 @@ namespace etics {
 constexpr int kMexThreads = 128;
 constexpr int kMexP = 8;                          // particles per thread (consecutive)
 constexpr int kMexTile = kMexThreads * kMexP;     // 1024
-constexpr int kMexLB = kMexLmaxLimit;             // compiled level bound (6)
-constexpr int kMexNC = (kMexLB + 1) * (kMexLB + 1);
+constexpr int kMexLB = kMexLmaxLimit;             // compiled level bound (10)
+constexpr int kMexNC = 49;                        // components of one level group, at most
+
+// Level groups: the per-thread moment arrays hold the components of one group
+// of levels, so that l_max up to kMexLB needs no more registers than l_max = 6.
+// A group's harmonics are recurred from level 0 (cheap next to the sums).
+constexpr int kMexGroups = 3;
+__host__ __device__ constexpr int mex_group_l0(int g) { return g == 0 ? 0 : (g == 1 ? 7 : 9); }
+__host__ __device__ constexpr int mex_group_l1(int g) { return g == 0 ? 6 : (g == 1 ? 8 : 10); }
+__host__ __device__ constexpr int mex_ncomp(int l_max) { return (l_max + 1) * (l_max + 1); }
+// components per side in the buffers: the l_max <= 6 kernels always use the
+// full 49 (zeros above l_max), so that their strides and loops are constants
+__host__ __device__ constexpr int mex_layout_ncomp(int l_max) {
+    return l_max <= 6 ? kMexNC : mex_ncomp(l_max);
+}
+static_assert(mex_group_l1(kMexGroups - 1) == kMexLB, "groups cover the compiled levels");
+static_assert(mex_ncomp(6) <= kMexNC && mex_ncomp(8) - mex_ncomp(6) <= kMexNC &&
+              mex_ncomp(10) - mex_ncomp(8) <= kMexNC, "group size");
+inline int mex_ngroups(int l_max) {
+    int g = 1;
+    while (g < kMexGroups && mex_group_l0(g) <= l_max) ++g;
+    return g;
+}
 
 inline int mex_tiles(int64_t N) { return (int)((N + kMexTile - 1) / kMexTile); }
 
@@ -81,32 +102,39 @@ __device__ __forceinline__ R harm_col(const R* C, const R* S, int c) {
     return c == 0 ? C[0] : ((c & 1) ? C[(c + 1) / 2] : S[c / 2]);
 }
 
-// ---- moments of one particle added to (ain, aout) ------------------------
-template <typename R, int L>
-__device__ __forceinline__ void mex_moments(R (&C)[3][kMexLB + 1], R (&S)[3][kMexLB + 1],
+// ---- moments of one particle added to (ain, aout): levels L0..L1 of the
+// group (component L*L + c at index L*L + c - L0*L0), levels below L0 only
+// recurred
+template <typename R, int L0, int L1, int L>
+__device__ __forceinline__ void mex_moments(R (&C)[3][L1 + 1], R (&S)[3][L1 + 1],
                                             const MexParticle<R>& pt, int l_max, R win, R wout,
                                             R irho, R (&ain)[kMexNC], R (&aout)[kMexNC]) {
-    if constexpr (L <= kMexLB) {
+    if constexpr (L <= L1) {
         if (L > l_max) return;
         constexpr int s0 = L % 3, s1 = (L + 2) % 3, s2 = (L + 1) % 3;
         harm_level<R, L>(C[s1], S[s1], C[s2], S[s2], pt.ux, pt.uy, pt.uz, pt.uu, C[s0], S[s0]);
+        if constexpr (L >= L0) {
+            constexpr int o = L * L - L0 * L0;
 #pragma unroll
-        for (int c = 0; c <= 2 * L; ++c) {
-            const R y = harm_col<R, L>(C[s0], S[s0], c);
-            ain[L * L + c] = fma(win, y, ain[L * L + c]);
-            aout[L * L + c] = fma(wout, y, aout[L * L + c]);
+            for (int c = 0; c <= 2 * L; ++c) {
+                const R y = harm_col<R, L>(C[s0], S[s0], c);
+                ain[o + c] = fma(win, y, ain[o + c]);
+                aout[o + c] = fma(wout, y, aout[o + c]);
+            }
         }
-        mex_moments<R, L + 1>(C, S, pt, l_max, win * pt.rho, wout * irho, irho, ain, aout);
+        mex_moments<R, L0, L1, L + 1>(C, S, pt, l_max, win * pt.rho, wout * irho, irho, ain,
+                                      aout);
     }
 }
 
-template <typename R>
+template <typename R, int L0, int L1>
 __device__ __forceinline__ void particle_moments(const MexParticle<R>& pt, int l_max,
                                                  R (&ain)[kMexNC], R (&aout)[kMexNC]) {
-    R C[3][kMexLB + 1], S[3][kMexLB + 1];
+    R C[3][L1 + 1], S[3][L1 + 1];
     const R irho = pt.origin ? R(0) : R(1) / pt.rho;
     // a particle at the origin has no outer moment (nothing lies inside it)
-    mex_moments<R, 0>(C, S, pt, l_max, pt.m, pt.origin ? R(0) : pt.m * irho, irho, ain, aout);
+    mex_moments<R, L0, L1, 0>(C, S, pt, l_max, pt.m, pt.origin ? R(0) : pt.m * irho, irho, ain,
+                              aout);
 }
 
 // ---- forward sweep, one particle: inner (q) part of the field, then q += own
@@ -115,84 +143,91 @@ __device__ __forceinline__ void particle_moments(const MexParticle<R>& pt, int l
 //   Phi_q = -(1/s) sum_l rho^-(l+1) sum_m w_lm q Y
 //   a_q   = (1/s^2) sum_l rho^-(l+2) sum_m w_lm q [G - (2l+1) Y u]
 // with Y, G the unnormalised harmonic and its gradient at the unit vector u.
-template <typename R, int L, bool ACC>
-__device__ __forceinline__ void mex_fwd(R (&C)[3][kMexLB + 1], R (&S)[3][kMexLB + 1],
+template <typename R, int L0, int L1, int L, bool ACC>
+__device__ __forceinline__ void mex_fwd(R (&C)[3][L1 + 1], R (&S)[3][L1 + 1],
                                         const MexParticle<R>& pt, int l_max, R win, R rinv,
                                         R irho, R (&q)[kMexNC], R& pot, R& ax, R& ay, R& az) {
-    if constexpr (L <= kMexLB) {
+    if constexpr (L <= L1) {
         if (L > l_max) return;
         constexpr int s0 = L % 3, s1 = (L + 2) % 3, s2 = (L + 1) % 3;
         harm_level<R, L>(C[s1], S[s1], C[s2], S[s2], pt.ux, pt.uy, pt.uz, pt.uu, C[s0], S[s0]);
-        if (!pt.origin) {
-            R P = R(0), vx = R(0), vy = R(0), vz = R(0);
-            R qc[L + 1], qs[L + 1];
+        if constexpr (L >= L0) {
+            constexpr int o = L * L - L0 * L0;
+            if (!pt.origin) {
+                R P = R(0), vx = R(0), vy = R(0), vz = R(0);
+                R qc[L + 1], qs[L + 1];
 #pragma unroll
-            for (int mm = 0; mm <= L; ++mm) {
-                const R w = mex_w<R>(L * (L + 1) / 2 + mm);
-                const int cc = L * L + (mm == 0 ? 0 : 2 * mm - 1);
-                qc[mm] = w * q[cc];
-                P = fma(qc[mm], C[s0][mm], P);
-                qs[mm] = R(0);
-                if (mm > 0) {
-                    qs[mm] = w * q[cc + 1];
-                    P = fma(qs[mm], S[s0][mm], P);
+                for (int mm = 0; mm <= L; ++mm) {
+                    const R w = mex_w<R>(L * (L + 1) / 2 + mm);
+                    const int cc = o + (mm == 0 ? 0 : 2 * mm - 1);
+                    qc[mm] = w * q[cc];
+                    P = fma(qc[mm], C[s0][mm], P);
+                    qs[mm] = R(0);
+                    if (mm > 0) {
+                        qs[mm] = w * q[cc + 1];
+                        P = fma(qs[mm], S[s0][mm], P);
+                    }
+                }
+                if (ACC && L >= 1) grad_contract<R, L>(C[s1], S[s1], qc, qs, vx, vy, vz);
+                pot = fma(rinv, P, pot);
+                if (ACC) {
+                    const R f = rinv * irho;
+                    const R k = R(2 * L + 1) * P;
+                    ax = fma(f, vx - k * pt.ux, ax);
+                    ay = fma(f, vy - k * pt.uy, ay);
+                    az = fma(f, vz - k * pt.uz, az);
                 }
             }
-            if (ACC && L >= 1) grad_contract<R, L>(C[s1], S[s1], qc, qs, vx, vy, vz);
-            pot = fma(rinv, P, pot);
-            if (ACC) {
-                const R f = rinv * irho;
-                const R k = R(2 * L + 1) * P;
-                ax = fma(f, vx - k * pt.ux, ax);
-                ay = fma(f, vy - k * pt.uy, ay);
-                az = fma(f, vz - k * pt.uz, az);
-            }
-        }
 #pragma unroll
-        for (int c = 0; c <= 2 * L; ++c)
-            q[L * L + c] = fma(win, harm_col<R, L>(C[s0], S[s0], c), q[L * L + c]);
-        mex_fwd<R, L + 1, ACC>(C, S, pt, l_max, win * pt.rho, rinv * irho, irho, q, pot, ax, ay, az);
+            for (int c = 0; c <= 2 * L; ++c)
+                q[o + c] = fma(win, harm_col<R, L>(C[s0], S[s0], c), q[o + c]);
+        }
+        mex_fwd<R, L0, L1, L + 1, ACC>(C, S, pt, l_max, win * pt.rho, rinv * irho, irho, q, pot,
+                                       ax, ay, az);
     }
 }
 
 // ---- reverse sweep, one particle: outer (p) part of the field, then p += own
 // outer moment.  On entry p is the outer sum over the particles after this one:
 //   Phi_p = -(1/s) sum_l rho^l sum_m w_lm p Y,   a_p = (1/s^2) sum_l rho^(l-1) sum_m w_lm p G
-template <typename R, int L, bool ACC>
-__device__ __forceinline__ void mex_rev(R (&C)[3][kMexLB + 1], R (&S)[3][kMexLB + 1],
+template <typename R, int L0, int L1, int L, bool ACC>
+__device__ __forceinline__ void mex_rev(R (&C)[3][L1 + 1], R (&S)[3][L1 + 1],
                                         const MexParticle<R>& pt, int l_max, R wout, R rl,
                                         R rlm1, R irho, R (&p)[kMexNC], R& pot, R& ax, R& ay,
                                         R& az) {
-    if constexpr (L <= kMexLB) {
+    if constexpr (L <= L1) {
         if (L > l_max) return;
         constexpr int s0 = L % 3, s1 = (L + 2) % 3, s2 = (L + 1) % 3;
         harm_level<R, L>(C[s1], S[s1], C[s2], S[s2], pt.ux, pt.uy, pt.uz, pt.uu, C[s0], S[s0]);
-        R P = R(0), vx = R(0), vy = R(0), vz = R(0);
-        R pc[L + 1], ps[L + 1];
+        if constexpr (L >= L0) {
+            constexpr int o = L * L - L0 * L0;
+            R P = R(0), vx = R(0), vy = R(0), vz = R(0);
+            R pc[L + 1], ps[L + 1];
 #pragma unroll
-        for (int mm = 0; mm <= L; ++mm) {
-            const R w = mex_w<R>(L * (L + 1) / 2 + mm);
-            const int cc = L * L + (mm == 0 ? 0 : 2 * mm - 1);
-            pc[mm] = w * p[cc];
-            P = fma(pc[mm], C[s0][mm], P);
-            ps[mm] = R(0);
-            if (mm > 0) {
-                ps[mm] = w * p[cc + 1];
-                P = fma(ps[mm], S[s0][mm], P);
+            for (int mm = 0; mm <= L; ++mm) {
+                const R w = mex_w<R>(L * (L + 1) / 2 + mm);
+                const int cc = o + (mm == 0 ? 0 : 2 * mm - 1);
+                pc[mm] = w * p[cc];
+                P = fma(pc[mm], C[s0][mm], P);
+                ps[mm] = R(0);
+                if (mm > 0) {
+                    ps[mm] = w * p[cc + 1];
+                    P = fma(ps[mm], S[s0][mm], P);
+                }
             }
-        }
-        if (ACC && L >= 1) grad_contract<R, L>(C[s1], S[s1], pc, ps, vx, vy, vz);
-        pot = fma(rl, P, pot);
-        if (ACC && L >= 1) {
-            ax = fma(rlm1, vx, ax);
-            ay = fma(rlm1, vy, ay);
-            az = fma(rlm1, vz, az);
-        }
+            if (ACC && L >= 1) grad_contract<R, L>(C[s1], S[s1], pc, ps, vx, vy, vz);
+            pot = fma(rl, P, pot);
+            if (ACC && L >= 1) {
+                ax = fma(rlm1, vx, ax);
+                ay = fma(rlm1, vy, ay);
+                az = fma(rlm1, vz, az);
+            }
 #pragma unroll
-        for (int c = 0; c <= 2 * L; ++c)
-            p[L * L + c] = fma(wout, harm_col<R, L>(C[s0], S[s0], c), p[L * L + c]);
-        mex_rev<R, L + 1, ACC>(C, S, pt, l_max, wout * irho, rl * pt.rho, rl, irho, p, pot, ax,
-                               ay, az);
+            for (int c = 0; c <= 2 * L; ++c)
+                p[o + c] = fma(wout, harm_col<R, L>(C[s0], S[s0], c), p[o + c]);
+        }
+        mex_rev<R, L0, L1, L + 1, ACC>(C, S, pt, l_max, wout * irho, rl * pt.rho, rl, irho, p,
+                                       pot, ax, ay, az);
     }
 }
 
@@ -233,16 +268,106 @@ __device__ __forceinline__ void scan_rows(R (&v)[kMexNC], R* buf, R* total, int 
 // ---------------------------------------------------------------------------
 // pass 1: gather into radial order + per-tile FP64 moment sums
 // ---------------------------------------------------------------------------
-template <typename R>
-// FP32: 4 blocks/SM (16 warps hide the gather latency); FP64 needs the registers
-__global__ void __launch_bounds__(kMexThreads, sizeof(R) == 4 ? 4 : 1)
+// resident blocks per SM the kernels' registers are sized for: FP32 with one
+// level group 4 (16 warps hide the gather latency); the multi-group kernels
+// and FP64 need more registers
+template <typename R, int NG>
+constexpr int mex_pass1_blocks() { return sizeof(R) == 4 ? (NG == 1 ? 4 : 2) : 1; }
+template <int NG>
+constexpr int mex_pass2_blocks() { return NG == 1 ? 4 : 2; }
+
+// One level group G of pass 1: this thread's moment sums over its kMexP
+// particles; their exclusive prefix (inner) and suffix (outer) over the tile,
+// by a transposed scan through shared memory (every thread writes its row of
+// sums, each lane scans one component serially down the 32 rows in lane
+// order, every thread reads its row back; the rows live where the particles
+// were); every thread's prefix and suffix stored, the tile's FP64 sums (tile
+// scale undone) stored.
+template <typename R, int NG, int G>
+__device__ __forceinline__ void mex_pass1_group(Vec4<R>* s_pt, R (*s_red)[2 * kMexNC],
+                                                const Vec4<R>* sorted, int64_t base, int nt,
+                                                int l_max, int e, R scale, double* tile_agg,
+                                                R* thread_sums, unsigned* err) {
+    constexpr int L0 = mex_group_l0(G), L1 = mex_group_l1(G);
+    if (L0 > l_max) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (G > 0) {
+        // the previous group's scan rows overwrote the particles
+        __syncthreads();
+        for (int i = tid; i < kMexTile; i += kMexThreads)
+            st4(&s_pt[mex_slot(i)], i < nt ? ld4(sorted + base + i) : mk4<R>(R(0), R(0), R(0), R(0)));
+        __syncthreads();
+    }
+    const int ncomp = NG == 1 ? kMexNC : mex_layout_ncomp(l_max);
+    const int c0 = L0 * L0;
+    // this group's components (all 49 for the single-group kernels)
+    const int gn = NG == 1 ? kMexNC : mex_ncomp(L1 < l_max ? L1 : l_max) - c0;
+    R ain[kMexNC], aout[kMexNC];
+#pragma unroll
+    for (int c = 0; c < kMexNC; ++c) { ain[c] = R(0); aout[c] = R(0); }
+#pragma unroll 1
+    for (int k = 0; k < kMexP; ++k) {
+        MexParticle<R> pt;
+        pt.init(s_pt[k * kMexThreads + tid], scale);
+        particle_moments<R, L0, L1>(pt, l_max, ain, aout);
+    }
+    static_assert(kMexThreads / 32 * 32 * kMexScanHalf * sizeof(R) <= kMexTile * sizeof(Vec4<R>),
+                  "scan rows");
+    __syncthreads();
+    R* rows = reinterpret_cast<R*>(s_pt) + warp * 32 * kMexScanHalf;
+    scan_rows<R, true>(ain, rows, &s_red[warp][0], lane);
+    scan_rows<R, false>(aout, rows, &s_red[warp][kMexNC], lane);
+    __syncthreads();
+    {
+        R* ts = thread_sums + (size_t)blockIdx.x * 2 * ncomp * kMexThreads + tid;
+#pragma unroll
+        for (int c = 0; c < kMexNC; ++c) {
+            if (c < gn) {
+                R q = R(0), pp = R(0);
+                for (int w = 0; w < warp; ++w) q += s_red[w][c];
+                for (int w = kMexThreads / 32 - 1; w > warp; --w) pp += s_red[w][kMexNC + c];
+                ts[(size_t)(c0 + c) * kMexThreads] = q + ain[c];
+                ts[(size_t)(ncomp + c0 + c) * kMexThreads] = pp + aout[c];
+            }
+        }
+    }
+    for (int c = tid; c < 2 * gn; c += kMexThreads) {
+        const bool inner = c < gn;
+        const int lc = inner ? c : c - gn;
+        double sum = 0.0;
+        for (int w = 0; w < kMexThreads / 32; ++w) sum += (double)s_red[w][(inner ? 0 : kMexNC) + lc];
+        const int cc = c0 + lc;
+        int l = 0;
+        while ((l + 1) * (l + 1) <= cc) ++l;
+        // undo the tile scale: inner moments scale as s^l, outer as s^-(l+1)
+        sum = inner ? ldexp(sum, l * e) : ldexp(sum, -(l + 1) * e);
+        if (!isfinite(sum)) report(err, ETICS_ERR_NONFINITE);
+        tile_agg[(size_t)blockIdx.x * 2 * ncomp + (inner ? 0 : ncomp) + cc] = sum;
+    }
+}
+
+template <typename R, int NG, int G>
+__device__ __forceinline__ void mex_pass1_groups(Vec4<R>* s_pt, R (*s_red)[2 * kMexNC],
+                                                 const Vec4<R>* sorted, int64_t base, int nt,
+                                                 int l_max, int e, R scale, double* tile_agg,
+                                                 R* thread_sums, unsigned* err) {
+    if constexpr (G < NG) {
+        mex_pass1_group<R, NG, G>(s_pt, s_red, sorted, base, nt, l_max, e, scale, tile_agg,
+                                  thread_sums, err);
+        mex_pass1_groups<R, NG, G + 1>(s_pt, s_red, sorted, base, nt, l_max, e, scale, tile_agg,
+                                       thread_sums, err);
+    }
+}
+
+template <typename R, int NG>
+__global__ void __launch_bounds__(kMexThreads, mex_pass1_blocks<R, NG>())
 mex_pass1_kernel(const Vec4<R>* __restrict__ posm, const uint32_t* __restrict__ perm, int64_t N,
                  int l_max, Vec4<R>* __restrict__ sorted, double* __restrict__ tile_agg,
                  R* __restrict__ thread_sums, unsigned* err) {
     __shared__ Vec4<R> s_pt[kMexTile];
     __shared__ R s_red[kMexThreads / 32][2 * kMexNC];
     pdl_wait();
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const int64_t base = (int64_t)blockIdx.x * kMexTile;
     const int64_t rem = N - base;
     const int nt = (int)(rem < kMexTile ? rem : kMexTile);
@@ -274,49 +399,49 @@ mex_pass1_kernel(const Vec4<R>* __restrict__ posm, const uint32_t* __restrict__ 
         e = tile_exponent<R>(radius<R>(a.x, a.y, a.z), radius<R>(b.x, b.y, b.z));
     }
     const R scale = ldexp(R(1), -e);
-    R ain[kMexNC], aout[kMexNC];
+    if constexpr (NG > 1) {
+        mex_pass1_groups<R, NG, 0>(s_pt, s_red, sorted, base, nt, l_max, e, scale, tile_agg,
+                                   thread_sums, err);
+    } else {
+        // l_max <= 6: the single group, written out (the same steps as
+        // mex_pass1_group with constant sizes)
+        const int lane = tid & 31, warp = tid >> 5;
+        R ain[kMexNC], aout[kMexNC];
 #pragma unroll
-    for (int c = 0; c < kMexNC; ++c) { ain[c] = R(0); aout[c] = R(0); }
+        for (int c = 0; c < kMexNC; ++c) { ain[c] = R(0); aout[c] = R(0); }
 #pragma unroll 1
-    for (int k = 0; k < kMexP; ++k) {
-        MexParticle<R> pt;
-        pt.init(s_pt[k * kMexThreads + tid], scale);
-        particle_moments<R>(pt, l_max, ain, aout);
-    }
-    // in-tile scans of the thread sums, per component: exclusive prefix
-    // (inner) and suffix (outer) over the lanes of each warp, transposed
-    // through shared memory: every thread writes its row of sums, each lane
-    // scans one component serially down the 32 rows (in lane order), every
-    // thread reads its row back.  Half of the components per round.  The
-    // warp totals go to s_red for the tile sums and the block-level combine.
-    // The rows live where the particles were (s_pt is no longer read).
-    static_assert(kMexThreads / 32 * 32 * kMexScanHalf * sizeof(R) <= sizeof(s_pt), "scan rows");
-    __syncthreads();
-    R* rows = reinterpret_cast<R*>(s_pt) + warp * 32 * kMexScanHalf;
-    scan_rows<R, true>(ain, rows, &s_red[warp][0], lane);
-    scan_rows<R, false>(aout, rows, &s_red[warp][kMexNC], lane);
-    __syncthreads();
-    {
-        R* ts = thread_sums + (size_t)blockIdx.x * 2 * kMexNC * kMexThreads + tid;
-#pragma unroll
-        for (int c = 0; c < kMexNC; ++c) {
-            R q = R(0), p = R(0);
-            for (int w = 0; w < warp; ++w) q += s_red[w][c];
-            for (int w = kMexThreads / 32 - 1; w > warp; --w) p += s_red[w][kMexNC + c];
-            ts[(size_t)c * kMexThreads] = q + ain[c];
-            ts[(size_t)(kMexNC + c) * kMexThreads] = p + aout[c];
+        for (int k = 0; k < kMexP; ++k) {
+            MexParticle<R> pt;
+            pt.init(s_pt[k * kMexThreads + tid], scale);
+            particle_moments<R, 0, 6>(pt, l_max, ain, aout);
         }
-    }
-    for (int c = tid; c < 2 * kMexNC; c += kMexThreads) {
-        double s = 0.0;
-        for (int w = 0; w < kMexThreads / 32; ++w) s += (double)s_red[w][c];
-        const int cc = c % kMexNC;
-        int l = 0;
-        while ((l + 1) * (l + 1) <= cc) ++l;
-        // undo the tile scale: inner moments scale as s^l, outer as s^-(l+1)
-        s = (c < kMexNC) ? ldexp(s, l * e) : ldexp(s, -(l + 1) * e);
-        if (!isfinite(s)) report(err, ETICS_ERR_NONFINITE);
-        tile_agg[(size_t)blockIdx.x * 2 * kMexNC + c] = s;
+        __syncthreads();
+        R* rows = reinterpret_cast<R*>(s_pt) + warp * 32 * kMexScanHalf;
+        scan_rows<R, true>(ain, rows, &s_red[warp][0], lane);
+        scan_rows<R, false>(aout, rows, &s_red[warp][kMexNC], lane);
+        __syncthreads();
+        {
+            R* ts = thread_sums + (size_t)blockIdx.x * 2 * kMexNC * kMexThreads + tid;
+#pragma unroll
+            for (int c = 0; c < kMexNC; ++c) {
+                R q = R(0), pp = R(0);
+                for (int w = 0; w < warp; ++w) q += s_red[w][c];
+                for (int w = kMexThreads / 32 - 1; w > warp; --w) pp += s_red[w][kMexNC + c];
+                ts[(size_t)c * kMexThreads] = q + ain[c];
+                ts[(size_t)(kMexNC + c) * kMexThreads] = pp + aout[c];
+            }
+        }
+        for (int c = tid; c < 2 * kMexNC; c += kMexThreads) {
+            double sum = 0.0;
+            for (int w = 0; w < kMexThreads / 32; ++w) sum += (double)s_red[w][c];
+            const int cc = c % kMexNC;
+            int l = 0;
+            while ((l + 1) * (l + 1) <= cc) ++l;
+            // undo the tile scale: inner moments scale as s^l, outer as s^-(l+1)
+            sum = (c < kMexNC) ? ldexp(sum, l * e) : ldexp(sum, -(l + 1) * e);
+            if (!isfinite(sum)) report(err, ETICS_ERR_NONFINITE);
+            tile_agg[(size_t)blockIdx.x * 2 * kMexNC + c] = sum;
+        }
     }
 }
 
@@ -326,18 +451,19 @@ mex_pass1_kernel(const Vec4<R>* __restrict__ posm, const uint32_t* __restrict__ 
 // ---------------------------------------------------------------------------
 constexpr int kCarryThreads = 1024;
 static __global__ void __launch_bounds__(kCarryThreads)
-mex_carry_kernel(const double* __restrict__ tile_agg, int ntiles, double* __restrict__ carry) {
+mex_carry_kernel(const double* __restrict__ tile_agg, int ntiles, int ncomp,
+                 double* __restrict__ carry) {
     __shared__ double s_w[kCarryThreads / 32];
     pdl_wait();
     const int c = blockIdx.x;
-    const bool rev = c >= kMexNC;
+    const bool rev = c >= ncomp;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int chunk = (ntiles + kCarryThreads - 1) / kCarryThreads;
     const int o0 = tid * chunk;
     auto tile_of = [&](int o) { return rev ? ntiles - 1 - o : o; };
     double local = 0.0;
     for (int o = o0; o < o0 + chunk && o < ntiles; ++o)
-        local += tile_agg[(size_t)tile_of(o) * 2 * kMexNC + c];
+        local += tile_agg[(size_t)tile_of(o) * 2 * ncomp + c];
     double x = local;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -352,82 +478,83 @@ mex_carry_kernel(const double* __restrict__ tile_agg, int ntiles, double* __rest
     if (lane == 0) ex = 0.0;
     run += ex;
     for (int o = o0; o < o0 + chunk && o < ntiles; ++o) {
-        const size_t idx = (size_t)tile_of(o) * 2 * kMexNC + c;
+        const size_t idx = (size_t)tile_of(o) * 2 * ncomp + c;
         carry[idx] = run;
         run += tile_agg[idx];
     }
 }
 
 // ---------------------------------------------------------------------------
-// pass 2: in-tile scans + field + scatter
+// pass 2: field from the exclusive sums, per level group
 // ---------------------------------------------------------------------------
-template <typename R, bool ACC>
-__global__ void __launch_bounds__(kMexThreads, 4)
-mex_pass2_kernel(const Vec4<R>* __restrict__ sorted, const uint32_t* __restrict__ perm, int64_t N,
-                 int l_max, const double* __restrict__ carry, const R* __restrict__ thread_sums,
-                 Vec4<R>* __restrict__ out, int out_mask, unsigned* err) {
-    __shared__ Vec4<R> s_pt[kMexTile];
-    __shared__ Vec4<R> s_f[kMexTile];   // inner part of each particle's field
-    __shared__ R s_q0[kMexNC], s_p0[kMexNC];
-    pdl_wait();
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t base = (int64_t)blockIdx.x * kMexTile;
-    const int64_t rem = N - base;
-    const int nt = (int)(rem < kMexTile ? rem : kMexTile);
-    for (int i = tid; i < kMexTile; i += kMexThreads)
-        st4(&s_pt[mex_slot(i)], i < nt ? ld4(sorted + base + i) : mk4<R>(R(0), R(0), R(0), R(0)));
-    __syncthreads();
-    int e;
-    {
-        const Vec4<R> a = s_pt[mex_slot(0)], b = s_pt[mex_slot(nt - 1)];
-        e = tile_exponent<R>(radius<R>(a.x, a.y, a.z), radius<R>(b.x, b.y, b.z));
-    }
-    const R scale = ldexp(R(1), -e);
-    for (int c = tid; c < 2 * kMexNC; c += kMexThreads) {
-        const int cc = c % kMexNC;
+// Group G: this thread's exclusive inner sum (tile carry + in-tile prefix from
+// pass 1), the forward sweep (inner part of the field, added to s_f), its
+// exclusive outer sum (a true suffix sum, never total minus prefix), the
+// reverse sweep (outer part); the last group present completes each
+// particle's field and scatters it back to the caller's order.
+template <typename R, int NG, int G, bool ACC>
+__device__ __forceinline__ void mex_pass2_group(const Vec4<R>* s_pt, Vec4<R>* s_f, R* s_q0,
+                                                R* s_p0, const double* carry,
+                                                const R* thread_sums, const uint32_t* perm,
+                                                int64_t base, int64_t N, int l_max, int e,
+                                                R scale, bool last, Vec4<R>* out, int out_mask,
+                                                unsigned* err) {
+    constexpr int L0 = mex_group_l0(G), L1 = mex_group_l1(G);
+    if (L0 > l_max) return;
+    const int tid = threadIdx.x;
+    const int ncomp = NG == 1 ? kMexNC : mex_layout_ncomp(l_max);
+    const int c0 = L0 * L0;
+    const int gn = NG == 1 ? kMexNC : mex_ncomp(L1 < l_max ? L1 : l_max) - c0;
+    if (G > 0) __syncthreads();   // the previous group's readers of s_q0 / s_p0 are done
+    for (int c = tid; c < 2 * gn; c += kMexThreads) {
+        const bool inner = c < gn;
+        const int lc = inner ? c : c - gn;
+        const int cc = c0 + lc;
         int l = 0;
         while ((l + 1) * (l + 1) <= cc) ++l;
-        const double v = carry[(size_t)blockIdx.x * 2 * kMexNC + c];
-        if (c < kMexNC) s_q0[cc] = (R)ldexp(v, -l * e);
-        else s_p0[cc] = (R)ldexp(v, (l + 1) * e);
+        const double v = carry[(size_t)blockIdx.x * 2 * ncomp + (inner ? 0 : ncomp) + cc];
+        if (inner) s_q0[lc] = (R)ldexp(v, -l * e);
+        else s_p0[lc] = (R)ldexp(v, (l + 1) * e);
     }
     __syncthreads();
-    // exclusive inner sum before this thread's first particle: the tile's
-    // carry plus this thread's in-tile prefix (pass 1); the outer sums are
-    // loaded only after the forward sweep, so the two 49-component arrays
-    // are never live at the same time
-    const R* ts = thread_sums + (size_t)blockIdx.x * 2 * kMexNC * kMexThreads + tid;
+    const R* ts = thread_sums + (size_t)blockIdx.x * 2 * ncomp * kMexThreads + tid;
     R a[kMexNC];
 #pragma unroll
-    for (int c = 0; c < kMexNC; ++c) a[c] = s_q0[c] + ts[(size_t)c * kMexThreads];
-    // forward sweep: inner part of the field, kept in shared memory
+    for (int c = 0; c < kMexNC; ++c)
+        a[c] = c < gn ? s_q0[c] + ts[(size_t)(c0 + c) * kMexThreads] : R(0);
 #pragma unroll 1
     for (int k = 0; k < kMexP; ++k) {
         MexParticle<R> pt;
         pt.init(s_pt[k * kMexThreads + tid], scale);
         const R irho = pt.origin ? R(0) : R(1) / pt.rho;
-        R C[3][kMexLB + 1], S[3][kMexLB + 1];
+        R C[3][L1 + 1], S[3][L1 + 1];
         R pot = R(0), ax = R(0), ay = R(0), az = R(0);
-        mex_fwd<R, 0, ACC>(C, S, pt, l_max, pt.m, irho, irho, a, pot, ax, ay, az);
+        if (G > 0) {
+            const Vec4<R> f = s_f[k * kMexThreads + tid];
+            ax = f.x; ay = f.y; az = f.z; pot = f.w;
+        }
+        mex_fwd<R, L0, L1, 0, ACC>(C, S, pt, l_max, pt.m, irho, irho, a, pot, ax, ay, az);
         st4(&s_f[k * kMexThreads + tid], mk4<R>(ax, ay, az, pot));
     }
-    // exclusive outer sum after this thread's last particle (a true suffix
-    // sum, never total minus prefix), then the reverse sweep which completes
-    // and scatters each particle
     R b[kMexNC];
 #pragma unroll
-    for (int c = 0; c < kMexNC; ++c) b[c] = s_p0[c] + ts[(size_t)(kMexNC + c) * kMexThreads];
+    for (int c = 0; c < kMexNC; ++c)
+        b[c] = c < gn ? s_p0[c] + ts[(size_t)(ncomp + c0 + c) * kMexThreads] : R(0);
     const R s1 = scale, s2 = scale * scale;
 #pragma unroll 1
     for (int k = kMexP - 1; k >= 0; --k) {
         MexParticle<R> pt;
         pt.init(s_pt[k * kMexThreads + tid], scale);
         const R irho = pt.origin ? R(0) : R(1) / pt.rho;
-        R C[3][kMexLB + 1], S[3][kMexLB + 1];
+        R C[3][L1 + 1], S[3][L1 + 1];
         const Vec4<R> f = s_f[k * kMexThreads + tid];
         R pot = f.w, ax = f.x, ay = f.y, az = f.z;
         const R wout = pt.origin ? R(0) : pt.m * irho;
-        mex_rev<R, 0, ACC>(C, S, pt, l_max, wout, R(1), R(0), irho, b, pot, ax, ay, az);
+        mex_rev<R, L0, L1, 0, ACC>(C, S, pt, l_max, wout, R(1), R(0), irho, b, pot, ax, ay, az);
+        if (!last) {
+            st4(&s_f[k * kMexThreads + tid], mk4<R>(ax, ay, az, pot));
+            continue;
+        }
         const int64_t i = base + (int64_t)tid * kMexP + k;
         if (i < N) {
             const R potv = (out_mask & ETICS_OUT_POT) ? -pot * s1 : R(0);
@@ -440,6 +567,48 @@ mex_pass2_kernel(const Vec4<R>* __restrict__ sorted, const uint32_t* __restrict_
     }
 }
 
+template <typename R, int NG, int G, bool ACC>
+__device__ __forceinline__ void mex_pass2_groups(const Vec4<R>* s_pt, Vec4<R>* s_f, R* s_q0,
+                                                 R* s_p0, const double* carry,
+                                                 const R* thread_sums, const uint32_t* perm,
+                                                 int64_t base, int64_t N, int l_max, int e,
+                                                 R scale, Vec4<R>* out, int out_mask,
+                                                 unsigned* err) {
+    if constexpr (G < NG) {
+        const bool last = G + 1 == NG || mex_group_l0(G + 1) > l_max;
+        mex_pass2_group<R, NG, G, ACC>(s_pt, s_f, s_q0, s_p0, carry, thread_sums, perm, base,
+                                       N, l_max, e, scale, last, out, out_mask, err);
+        mex_pass2_groups<R, NG, G + 1, ACC>(s_pt, s_f, s_q0, s_p0, carry, thread_sums, perm,
+                                            base, N, l_max, e, scale, out, out_mask, err);
+    }
+}
+
+template <typename R, int NG, bool ACC>
+__global__ void __launch_bounds__(kMexThreads, mex_pass2_blocks<NG>())
+mex_pass2_kernel(const Vec4<R>* __restrict__ sorted, const uint32_t* __restrict__ perm, int64_t N,
+                 int l_max, const double* __restrict__ carry, const R* __restrict__ thread_sums,
+                 Vec4<R>* __restrict__ out, int out_mask, unsigned* err) {
+    __shared__ Vec4<R> s_pt[kMexTile];
+    __shared__ Vec4<R> s_f[kMexTile];   // each particle's field so far
+    __shared__ R s_q0[kMexNC], s_p0[kMexNC];
+    pdl_wait();
+    const int tid = threadIdx.x;
+    const int64_t base = (int64_t)blockIdx.x * kMexTile;
+    const int64_t rem = N - base;
+    const int nt = (int)(rem < kMexTile ? rem : kMexTile);
+    for (int i = tid; i < kMexTile; i += kMexThreads)
+        st4(&s_pt[mex_slot(i)], i < nt ? ld4(sorted + base + i) : mk4<R>(R(0), R(0), R(0), R(0)));
+    __syncthreads();
+    int e;
+    {
+        const Vec4<R> a = s_pt[mex_slot(0)], b = s_pt[mex_slot(nt - 1)];
+        e = tile_exponent<R>(radius<R>(a.x, a.y, a.z), radius<R>(b.x, b.y, b.z));
+    }
+    const R scale = ldexp(R(1), -e);
+    mex_pass2_groups<R, NG, 0, ACC>(s_pt, s_f, s_q0, s_p0, carry, thread_sums, perm, base, N,
+                                    l_max, e, scale, out, out_mask, err);
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -447,13 +616,14 @@ template <typename R>
 struct MexBuffers {
     SortBuffers sort;
     Vec4<R>* sorted;
-    double* tile_agg;
-    double* carry;
-    R* thread_sums;      // [tile][2 * kMexNC][kMexThreads], in-tile exclusive prefix / suffix
+    double* tile_agg;    // [tile][2 * ncomp]: inner then outer sums (ncomp: mex_layout_ncomp)
+    double* carry;       // [tile][2 * ncomp]
+    R* thread_sums;      // [tile][2 * ncomp][kMexThreads], in-tile exclusive prefix / suffix
 };
 
+// ncomp = mex_layout_ncomp(l_max) components per side
 template <typename R>
-inline MexBuffers<R> mex_buffers(void* ws, int64_t N, size_t* total) {
+inline MexBuffers<R> mex_buffers(void* ws, int64_t N, int l_max, size_t* total) {
     MexBuffers<R> b{};
     size_t off = 0;
     b.sort = sort_buffers(ws, N, &off);
@@ -465,48 +635,44 @@ inline MexBuffers<R> mex_buffers(void* ws, int64_t N, size_t* total) {
     };
     const size_t n = (size_t)(N > 0 ? N : 1);
     const size_t nt = (size_t)(mex_tiles(N) > 0 ? mex_tiles(N) : 1);
+    const size_t nc = (size_t)mex_layout_ncomp(l_max > 0 ? l_max : 0);
     b.sorted = reinterpret_cast<Vec4<R>*>(take(n * sizeof(Vec4<R>)));
-    b.tile_agg = reinterpret_cast<double*>(take(nt * 2 * kMexNC * sizeof(double)));
-    b.carry = reinterpret_cast<double*>(take(nt * 2 * kMexNC * sizeof(double)));
-    b.thread_sums = reinterpret_cast<R*>(take(nt * 2 * kMexNC * kMexThreads * sizeof(R)));
+    b.tile_agg = reinterpret_cast<double*>(take(nt * 2 * nc * sizeof(double)));
+    b.carry = reinterpret_cast<double*>(take(nt * 2 * nc * sizeof(double)));
+    b.thread_sums = reinterpret_cast<R*>(take(nt * 2 * nc * kMexThreads * sizeof(R)));
     if (total) *total = off;
     return b;
 }
 
 template <typename R>
-inline size_t mex_workspace_impl(int64_t N) {
+inline size_t mex_workspace_impl(int64_t N, int l_max) {
     size_t total = 0;
-    mex_buffers<R>(nullptr, N, &total);
+    mex_buffers<R>(nullptr, N, l_max, &total);
     return total;
 }
 
-template <typename R>
-inline int mex_field_impl(const void* posm, int64_t N, int l_max, void* out, int out_mask,
-                          void* ws, const LaunchCtx& ctx) {
-    if (N == 0) return ETICS_OK;
-    MexBuffers<R> b = mex_buffers<R>(ws, N, nullptr);
-    stage_event(ctx, 0);
-    int rc = radial_sort_impl<R>(posm, N, b.sort, ctx);
-    if (rc) return rc;
-    stage_event(ctx, 2);
+template <typename R, int NG>
+inline int mex_passes(const MexBuffers<R>& b, const Vec4<R>* pp, int64_t N, int l_max, void* out,
+                      int out_mask, const LaunchCtx& ctx) {
     const int nt = mex_tiles(N);
-    const Vec4<R>* pp = reinterpret_cast<const Vec4<R>*>(posm);
-    if (launch_pdl(mex_pass1_kernel<R>, dim3(nt), dim3(kMexThreads), 0, ctx.stream, pp,
-                   (const uint32_t*)b.sort.vals_a, N, l_max, b.sorted, b.tile_agg, b.thread_sums, ctx.err))
+    const int ncomp = mex_layout_ncomp(l_max);
+    if (launch_pdl(mex_pass1_kernel<R, NG>, dim3(nt), dim3(kMexThreads), 0, ctx.stream, pp,
+                   (const uint32_t*)b.sort.vals_a, N, l_max, b.sorted, b.tile_agg, b.thread_sums,
+                   ctx.err))
         return ETICS_ERR_CUDA;
     ++*ctx.launches;
     stage_event(ctx, 3);
-    if (launch_pdl(mex_carry_kernel, dim3(2 * kMexNC), dim3(kCarryThreads), 0, ctx.stream,
-                   (const double*)b.tile_agg, nt, b.carry))
+    if (launch_pdl(mex_carry_kernel, dim3(2 * ncomp), dim3(kCarryThreads), 0, ctx.stream,
+                   (const double*)b.tile_agg, nt, ncomp, b.carry))
         return ETICS_ERR_CUDA;
     ++*ctx.launches;
     stage_event(ctx, 4);
     Vec4<R>* op = reinterpret_cast<Vec4<R>*>(out);
     const cudaError_t le = (out_mask & ETICS_OUT_ACC)
-        ? launch_pdl(mex_pass2_kernel<R, true>, dim3(nt), dim3(kMexThreads), 0, ctx.stream,
+        ? launch_pdl(mex_pass2_kernel<R, NG, true>, dim3(nt), dim3(kMexThreads), 0, ctx.stream,
                      (const Vec4<R>*)b.sorted, (const uint32_t*)b.sort.vals_a, N, l_max,
                      (const double*)b.carry, (const R*)b.thread_sums, op, out_mask, ctx.err)
-        : launch_pdl(mex_pass2_kernel<R, false>, dim3(nt), dim3(kMexThreads), 0, ctx.stream,
+        : launch_pdl(mex_pass2_kernel<R, NG, false>, dim3(nt), dim3(kMexThreads), 0, ctx.stream,
                      (const Vec4<R>*)b.sorted, (const uint32_t*)b.sort.vals_a, N, l_max,
                      (const double*)b.carry, (const R*)b.thread_sums, op, out_mask, ctx.err);
     if (le) return ETICS_ERR_CUDA;
@@ -516,10 +682,25 @@ inline int mex_field_impl(const void* posm, int64_t N, int l_max, void* out, int
 }
 
 template <typename R>
+inline int mex_field_impl(const void* posm, int64_t N, int l_max, void* out, int out_mask,
+                          void* ws, const LaunchCtx& ctx) {
+    if (N == 0) return ETICS_OK;
+    MexBuffers<R> b = mex_buffers<R>(ws, N, l_max, nullptr);
+    stage_event(ctx, 0);
+    int rc = radial_sort_impl<R>(posm, N, b.sort, ctx);
+    if (rc) return rc;
+    stage_event(ctx, 2);
+    const Vec4<R>* pp = reinterpret_cast<const Vec4<R>*>(posm);
+    // l_max <= 6: one level group (the kernels specialised for it)
+    if (mex_ngroups(l_max) == 1) return mex_passes<R, 1>(b, pp, N, l_max, out, out_mask, ctx);
+    return mex_passes<R, kMexGroups>(b, pp, N, l_max, out, out_mask, ctx);
+}
+
+template <typename R>
 inline int radial_order_impl(const void* posm, int64_t N, uint32_t* order, void* ws,
                              const LaunchCtx& ctx) {
     if (N == 0) return ETICS_OK;
-    MexBuffers<R> b = mex_buffers<R>(ws, N, nullptr);
+    MexBuffers<R> b = mex_buffers<R>(ws, N, 0, nullptr);
     int rc = radial_sort_impl<R>(posm, N, b.sort, ctx);
     if (rc) return rc;
     if (cudaMemcpyAsync(order, b.sort.vals_a, (size_t)N * 4, cudaMemcpyDeviceToDevice, ctx.stream))

@@ -22,7 +22,7 @@ from . import build as _build
 SCF, MEX = 0, 1
 FP64, MIXED = 0, 1
 OUT_ACC, OUT_POT = 1, 2
-NMAX_LIMIT, LMAX_LIMIT, MEX_LMAX_LIMIT = 16, 14, 6
+NMAX_LIMIT, LMAX_LIMIT, MEX_LMAX_LIMIT = 16, 14, 10
 
 _STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA runtime error", -3: "workspace too small",
            -4: "non-finite input or FP32 overflow", -5: "inter-block wait timed out",

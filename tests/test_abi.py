@@ -53,7 +53,7 @@ def test_argument_errors_are_synchronous(lib):
     # limits
     assert lib.etics_scf_coeffs(fake, 10, 17, 2, 1, fake, fake, 0, None) == -6
     assert lib.etics_scf_field(fake, 10, 4, 15, 1, fake, fake, 3, None) == -6
-    assert lib.etics_mex_field(fake, 10, 7, 1, fake, 3, fake, 0, None) == -6
+    assert lib.etics_mex_field(fake, 10, 11, 1, fake, 3, fake, 0, None) == -6
     # empty output mask
     assert lib.etics_scf_field(fake, 10, 4, 2, 1, fake, fake, 0, None) == -1
     assert lib.etics_strerror(-3) == b"workspace too small"

@@ -150,7 +150,7 @@ def test_radial_order_full_size(precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-@pytest.mark.parametrize("l_max", [6, 4, 2, 1, 0])
+@pytest.mark.parametrize("l_max", [10, 9, 8, 7, 6, 4, 2, 1, 0])
 def test_field_matches_oracle(precision, l_max):
     pm = hernquist(12345, seed=11)
     ref_in = rounded(pm, precision)
@@ -176,7 +176,7 @@ def test_edge_cases(precision):
     big[100:140, 3] *= rng.uniform(0.5, 2.0, 40)
     cases.append(big)
     for pm in cases:
-        for l_max in [6, 3, 0]:
+        for l_max in [10, 7, 6, 3, 0]:
             ref_in = rounded(pm, precision)
             acc_ref, pot_ref, _ = oracle.mex_field(ref_in[:, :3], ref_in[:, 3], l_max)
             o = etics.mex_field(device_particles(pm, precision), l_max).cpu().numpy()
