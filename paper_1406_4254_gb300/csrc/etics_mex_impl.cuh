@@ -276,89 +276,6 @@ constexpr int mex_pass1_blocks() { return sizeof(R) == 4 ? (NG == 1 ? 4 : 2) : 1
 template <int NG>
 constexpr int mex_pass2_blocks() { return NG == 1 ? 4 : 2; }
 
-// One level group G of pass 1: this thread's moment sums over its kMexP
-// particles; their exclusive prefix (inner) and suffix (outer) over the tile,
-// by a transposed scan through shared memory (every thread writes its row of
-// sums, each lane scans one component serially down the 32 rows in lane
-// order, every thread reads its row back; the rows live where the particles
-// were); every thread's prefix and suffix stored, the tile's FP64 sums (tile
-// scale undone) stored.
-template <typename R, int NG, int G>
-__device__ __forceinline__ void mex_pass1_group(Vec4<R>* s_pt, R (*s_red)[2 * kMexNC],
-                                                const Vec4<R>* sorted, int64_t base, int nt,
-                                                int l_max, int e, R scale, double* tile_agg,
-                                                R* thread_sums, unsigned* err) {
-    constexpr int L0 = mex_group_l0(G), L1 = mex_group_l1(G);
-    if (L0 > l_max) return;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (G > 0) {
-        // the previous group's scan rows overwrote the particles
-        __syncthreads();
-        for (int i = tid; i < kMexTile; i += kMexThreads)
-            st4(&s_pt[mex_slot(i)], i < nt ? ld4(sorted + base + i) : mk4<R>(R(0), R(0), R(0), R(0)));
-        __syncthreads();
-    }
-    const int ncomp = NG == 1 ? kMexNC : mex_layout_ncomp(l_max);
-    const int c0 = L0 * L0;
-    // this group's components (all 49 for the single-group kernels)
-    const int gn = NG == 1 ? kMexNC : mex_ncomp(L1 < l_max ? L1 : l_max) - c0;
-    R ain[kMexNC], aout[kMexNC];
-#pragma unroll
-    for (int c = 0; c < kMexNC; ++c) { ain[c] = R(0); aout[c] = R(0); }
-#pragma unroll 1
-    for (int k = 0; k < kMexP; ++k) {
-        MexParticle<R> pt;
-        pt.init(s_pt[k * kMexThreads + tid], scale);
-        particle_moments<R, L0, L1>(pt, l_max, ain, aout);
-    }
-    static_assert(kMexThreads / 32 * 32 * kMexScanHalf * sizeof(R) <= kMexTile * sizeof(Vec4<R>),
-                  "scan rows");
-    __syncthreads();
-    R* rows = reinterpret_cast<R*>(s_pt) + warp * 32 * kMexScanHalf;
-    scan_rows<R, true>(ain, rows, &s_red[warp][0], lane);
-    scan_rows<R, false>(aout, rows, &s_red[warp][kMexNC], lane);
-    __syncthreads();
-    {
-        R* ts = thread_sums + (size_t)blockIdx.x * 2 * ncomp * kMexThreads + tid;
-#pragma unroll
-        for (int c = 0; c < kMexNC; ++c) {
-            if (c < gn) {
-                R q = R(0), pp = R(0);
-                for (int w = 0; w < warp; ++w) q += s_red[w][c];
-                for (int w = kMexThreads / 32 - 1; w > warp; --w) pp += s_red[w][kMexNC + c];
-                ts[(size_t)(c0 + c) * kMexThreads] = q + ain[c];
-                ts[(size_t)(ncomp + c0 + c) * kMexThreads] = pp + aout[c];
-            }
-        }
-    }
-    for (int c = tid; c < 2 * gn; c += kMexThreads) {
-        const bool inner = c < gn;
-        const int lc = inner ? c : c - gn;
-        double sum = 0.0;
-        for (int w = 0; w < kMexThreads / 32; ++w) sum += (double)s_red[w][(inner ? 0 : kMexNC) + lc];
-        const int cc = c0 + lc;
-        int l = 0;
-        while ((l + 1) * (l + 1) <= cc) ++l;
-        // undo the tile scale: inner moments scale as s^l, outer as s^-(l+1)
-        sum = inner ? ldexp(sum, l * e) : ldexp(sum, -(l + 1) * e);
-        if (!isfinite(sum)) report(err, ETICS_ERR_NONFINITE);
-        tile_agg[(size_t)blockIdx.x * 2 * ncomp + (inner ? 0 : ncomp) + cc] = sum;
-    }
-}
-
-template <typename R, int NG, int G>
-__device__ __forceinline__ void mex_pass1_groups(Vec4<R>* s_pt, R (*s_red)[2 * kMexNC],
-                                                 const Vec4<R>* sorted, int64_t base, int nt,
-                                                 int l_max, int e, R scale, double* tile_agg,
-                                                 R* thread_sums, unsigned* err) {
-    if constexpr (G < NG) {
-        mex_pass1_group<R, NG, G>(s_pt, s_red, sorted, base, nt, l_max, e, scale, tile_agg,
-                                  thread_sums, err);
-        mex_pass1_groups<R, NG, G + 1>(s_pt, s_red, sorted, base, nt, l_max, e, scale, tile_agg,
-                                       thread_sums, err);
-    }
-}
-
 template <typename R, int NG>
 __global__ void __launch_bounds__(kMexThreads, mex_pass1_blocks<R, NG>())
 mex_pass1_kernel(const Vec4<R>* __restrict__ posm, const uint32_t* __restrict__ perm, int64_t N,
@@ -399,13 +316,29 @@ mex_pass1_kernel(const Vec4<R>* __restrict__ posm, const uint32_t* __restrict__ 
         e = tile_exponent<R>(radius<R>(a.x, a.y, a.z), radius<R>(b.x, b.y, b.z));
     }
     const R scale = ldexp(R(1), -e);
-    if constexpr (NG > 1) {
-        mex_pass1_groups<R, NG, 0>(s_pt, s_red, sorted, base, nt, l_max, e, scale, tile_agg,
-                                   thread_sums, err);
-    } else {
-        // l_max <= 6: the single group, written out (the same steps as
-        // mex_pass1_group with constant sizes)
-        const int lane = tid & 31, warp = tid >> 5;
+    const int lane = tid & 31, warp = tid >> 5;
+    // One level group per iteration: this thread's moment sums over its kMexP
+    // particles; their exclusive prefix (inner) and suffix (outer) over the
+    // tile, by a transposed scan through shared memory (every thread writes
+    // its row of sums, each lane scans one component serially down the 32
+    // rows in lane order, every thread reads its row back; the rows live
+    // where the particles were); every thread's prefix and suffix stored, the
+    // tile's FP64 sums (tile scale undone) stored.  l_max <= 6 is the single
+    // group with constant sizes.
+    const int ncomp = NG == 1 ? kMexNC : mex_layout_ncomp(l_max);
+    for (int g = 0; g < NG; ++g) {
+        const int L0 = mex_group_l0(g), L1 = mex_group_l1(g);
+        if (L0 > l_max) break;
+        if (g > 0) {
+            // the previous group's scan rows overwrote the particles
+            __syncthreads();
+            for (int i = tid; i < kMexTile; i += kMexThreads)
+                st4(&s_pt[mex_slot(i)],
+                    i < nt ? ld4(sorted + base + i) : mk4<R>(R(0), R(0), R(0), R(0)));
+            __syncthreads();
+        }
+        const int c0 = L0 * L0;
+        const int gn = NG == 1 ? kMexNC : mex_ncomp(L1 < l_max ? L1 : l_max) - c0;
         R ain[kMexNC], aout[kMexNC];
 #pragma unroll
         for (int c = 0; c < kMexNC; ++c) { ain[c] = R(0); aout[c] = R(0); }
@@ -413,34 +346,42 @@ mex_pass1_kernel(const Vec4<R>* __restrict__ posm, const uint32_t* __restrict__ 
         for (int k = 0; k < kMexP; ++k) {
             MexParticle<R> pt;
             pt.init(s_pt[k * kMexThreads + tid], scale);
-            particle_moments<R, 0, 6>(pt, l_max, ain, aout);
+            if (NG == 1 || g == 0) particle_moments<R, 0, 6>(pt, l_max, ain, aout);
+            else if (g == 1) particle_moments<R, 7, 8>(pt, l_max, ain, aout);
+            else particle_moments<R, 9, 10>(pt, l_max, ain, aout);
         }
+        static_assert(kMexThreads / 32 * 32 * kMexScanHalf * sizeof(R) <= sizeof(s_pt), "rows");
         __syncthreads();
         R* rows = reinterpret_cast<R*>(s_pt) + warp * 32 * kMexScanHalf;
         scan_rows<R, true>(ain, rows, &s_red[warp][0], lane);
         scan_rows<R, false>(aout, rows, &s_red[warp][kMexNC], lane);
         __syncthreads();
         {
-            R* ts = thread_sums + (size_t)blockIdx.x * 2 * kMexNC * kMexThreads + tid;
+            R* ts = thread_sums + (size_t)blockIdx.x * 2 * ncomp * kMexThreads + tid;
 #pragma unroll
             for (int c = 0; c < kMexNC; ++c) {
-                R q = R(0), pp = R(0);
-                for (int w = 0; w < warp; ++w) q += s_red[w][c];
-                for (int w = kMexThreads / 32 - 1; w > warp; --w) pp += s_red[w][kMexNC + c];
-                ts[(size_t)c * kMexThreads] = q + ain[c];
-                ts[(size_t)(kMexNC + c) * kMexThreads] = pp + aout[c];
+                if (c < gn) {
+                    R q = R(0), pp = R(0);
+                    for (int w = 0; w < warp; ++w) q += s_red[w][c];
+                    for (int w = kMexThreads / 32 - 1; w > warp; --w) pp += s_red[w][kMexNC + c];
+                    ts[(size_t)(c0 + c) * kMexThreads] = q + ain[c];
+                    ts[(size_t)(ncomp + c0 + c) * kMexThreads] = pp + aout[c];
+                }
             }
         }
-        for (int c = tid; c < 2 * kMexNC; c += kMexThreads) {
+        for (int c = tid; c < 2 * gn; c += kMexThreads) {
+            const bool inner = c < gn;
+            const int lc = inner ? c : c - gn;
             double sum = 0.0;
-            for (int w = 0; w < kMexThreads / 32; ++w) sum += (double)s_red[w][c];
-            const int cc = c % kMexNC;
+            for (int w = 0; w < kMexThreads / 32; ++w)
+                sum += (double)s_red[w][(inner ? 0 : kMexNC) + lc];
+            const int cc = c0 + lc;
             int l = 0;
             while ((l + 1) * (l + 1) <= cc) ++l;
             // undo the tile scale: inner moments scale as s^l, outer as s^-(l+1)
-            sum = (c < kMexNC) ? ldexp(sum, l * e) : ldexp(sum, -(l + 1) * e);
+            sum = inner ? ldexp(sum, l * e) : ldexp(sum, -(l + 1) * e);
             if (!isfinite(sum)) report(err, ETICS_ERR_NONFINITE);
-            tile_agg[(size_t)blockIdx.x * 2 * kMexNC + c] = sum;
+            tile_agg[(size_t)blockIdx.x * 2 * ncomp + (inner ? 0 : ncomp) + cc] = sum;
         }
     }
 }
