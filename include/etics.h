@@ -114,9 +114,13 @@ int etics_scf_field_basis(const void *posm, int64_t N, int n_max, int l_max, int
  * and outer exclusive cumulative sums of m r^l Y_lm and m r^-(l+1) Y_lm, and
  * Phi_i = -sum_l 4pi/(2l+1) sum_m [q_lm(i) r^-(l+1) + p_lm(i) r^l] Y_lm(x_i).
  * The order is by r^2 = (x*x + y*y) + z*z evaluated in FP64 (bitwise as a
- * CPU evaluates it), ties by particle index.  A particle at the origin sorts
- * first, contributes no outer moment, and feels only the outer l <= 1 field.
- * ws: at least etics_workspace_bytes(N, 0, l_max, ETICS_MEX, p). */
+ * CPU evaluates it), ties by particle index, with no limit on how many
+ * particles share a radius (a shell).  A particle at the origin sorts first,
+ * contributes no outer moment, and feels only the outer l <= 1 field.
+ * 0 <= l_max <= ETICS_MEX_LMAX_LIMIT; levels above 6 run in level groups
+ * (more time, the same registers).
+ * ws: at least etics_workspace_bytes(N, 0, l_max, ETICS_MEX, p) (it grows
+ * with (l_max+1)^2 above l_max = 6). */
 int etics_mex_field(const void *posm, int64_t N, int l_max, int precision, void *accpot,
                     int out_mask, void *ws, size_t ws_bytes, void *stream);
 
