@@ -270,11 +270,11 @@ __device__ __forceinline__ void scan_rows(R (&v)[kMexNC], R* buf, R* total, int 
 // ---------------------------------------------------------------------------
 // resident blocks per SM the kernels' registers are sized for: FP32 with one
 // level group 4 (16 warps hide the gather latency); the multi-group kernels
-// and FP64 need more registers
+// and FP64 need more registers (FP64 pass 2 at 4 blocks spilled ~1 KB)
 template <typename R, int NG>
 constexpr int mex_pass1_blocks() { return sizeof(R) == 4 ? (NG == 1 ? 4 : 2) : 1; }
-template <int NG>
-constexpr int mex_pass2_blocks() { return NG == 1 ? 4 : 2; }
+template <typename R, int NG>
+constexpr int mex_pass2_blocks() { return sizeof(R) == 4 ? (NG == 1 ? 4 : 2) : (NG == 1 ? 2 : 1); }
 
 template <typename R, int NG>
 __global__ void __launch_bounds__(kMexThreads, mex_pass1_blocks<R, NG>())
@@ -525,7 +525,7 @@ __device__ __forceinline__ void mex_pass2_groups(const Vec4<R>* s_pt, Vec4<R>* s
 }
 
 template <typename R, int NG, bool ACC>
-__global__ void __launch_bounds__(kMexThreads, mex_pass2_blocks<NG>())
+__global__ void __launch_bounds__(kMexThreads, mex_pass2_blocks<R, NG>())
 mex_pass2_kernel(const Vec4<R>* __restrict__ sorted, const uint32_t* __restrict__ perm, int64_t N,
                  int l_max, const double* __restrict__ carry, const R* __restrict__ thread_sums,
                  Vec4<R>* __restrict__ out, int out_mask, unsigned* err) {
