@@ -229,13 +229,15 @@ def test_deterministic():
     assert torch.equal(a, b)
 
 
-def test_full_size_bench_config():
-    """N = 2^20 flattened Hernquist (1 : 0.8 : 0.6), l_max = 6, mixed path:
-    every particle against the oracle."""
+@pytest.mark.parametrize("l_max", [6, 10])
+def test_full_size_bench_config(l_max):
+    """N = 2^20 flattened Hernquist (1 : 0.8 : 0.6), mixed path, every
+    particle against the oracle: l_max = 6 (the benchmark) and 10 (all three
+    level groups)."""
     n = 1 << 20
     pm = hernquist(n, seed=0)
     ref_in = rounded(pm, "mixed")
-    acc_ref, pot_ref, _ = oracle.mex_field(ref_in[:, :3], ref_in[:, 3], 6)
-    o = etics.mex_field(device_particles(pm, "mixed"), 6).cpu().numpy()
+    acc_ref, pot_ref, _ = oracle.mex_field(ref_in[:, :3], ref_in[:, 3], l_max)
+    o = etics.mex_field(device_particles(pm, "mixed"), l_max).cpu().numpy()
     etics.check_error()
-    assert_field_close(o, acc_ref, pot_ref, "mixed", "mex 2^20")
+    assert_field_close(o, acc_ref, pot_ref, "mixed", f"mex 2^20 l={l_max}")
