@@ -402,13 +402,14 @@ def accuracy(x, out_scf, out_mex):
             "scf": st(eps(out_scf, a_scf)), "mex": st(eps(out_mex, a_mex))}
 
 
-def oracle_step_time(pm_sample):
-    """Wall time of one oracle SCF (coeffs + field) and one MEX calculation."""
+def oracle_step_time(pm_sample, nthreads=0):
+    """Wall time of one oracle SCF (coeffs + field) and one MEX calculation
+    (nthreads for the field pass, the oracle's one threaded part; 0 = all)."""
     import oracle
     x, m = pm_sample[:, :3], pm_sample[:, 3]
     t0 = time.perf_counter()
     c = oracle.scf_coeffs(x, m, N_MAX, L_MAX)
-    oracle.scf_field(x, N_MAX, L_MAX, c)
+    oracle.scf_field(x, N_MAX, L_MAX, c, nthreads=nthreads)
     t1 = time.perf_counter()
     oracle.mex_field(x, m, L_MAX)
     t2 = time.perf_counter()
@@ -421,10 +422,13 @@ def cpu_baseline(n_sample, repeats, seed=0):
     pm = inputs.hernquist(n_sample, seed=seed, axes=(1.0, 0.8, 0.6))
     ts = [oracle_step_time(pm) for _ in range(repeats)]
     t = statistics.mean(a + b for a, b in ts)
+    # one core, for comparison with the paper's one-core CPU figure (Sec. 3.4)
+    t1 = sum(oracle_step_time(pm, nthreads=1))
     return {"value": 2 * n_sample / t, "unit": UNIT, "cores": oracle.default_threads(),
             "kind": "oracle",
             "sample": (f"{n_sample} particles of the same model, {repeats} steps; SCF field pass "
-                       f"threaded over particles, SCF coefficient and MEX passes serial")}
+                       f"threaded over particles, SCF coefficient and MEX passes serial"),
+            "single_core": {"value": 2 * n_sample / t1, "unit": UNIT, "cores": 1}}
 
 
 def run_leapfrog(args):
