@@ -1,6 +1,7 @@
 // etics_scf_bins_f32.cu -- the per-warp-bin SCF coefficient pass (see
-// etics_scf_bins.cuh) at (n_max, l_max) = (14, 8), the expansion of the
-// paper's bar-perturbed Hernquist runs (Sec. 4).  12 bins of at most 7
+// etics_scf_bins.cuh) at (n_max, l_max) = (14, 8), the expansion the
+// surrogate experiment uses for its bar-perturbed Hernquist sphere (the
+// coefficients of Sec. 2.4 eq. 18 in the basis of Sec. 2.5).  12 bins of at most 7
 // columns: 384 threads, 105 FP32 accumulators per lane, so one block per SM;
 // tiles of 192 particles keep the two 81-column basis buffers within shared
 // memory.  Its own translation unit so that it compiles in parallel with the
