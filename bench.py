@@ -757,9 +757,9 @@ def run_accuracy(args):
     their polynomial potential recomputed from the 1-D index-symbol
     integrals, and the closed-form Hernquist and Plummer spheres.  N from
     10^3 to 10^6; realisations are stacked up to 10^6 particles per point (at
-    most 100).  MEX at even l_max = 0..10 (the paper's Figs. 4 and 5); SCF at
+    most 100).  MEX at even l_max = 0..10 (the paper's Figs. 8 and 9); SCF at
     l_max = 6 with n_max = 0..14 and at l_max = 10 with n_max = 6, 10, 14
-    (the paper's Fig. 8 sweep, where SCF approaches MEX as n_max grows), and
+    (the paper's Fig. 10 sweep, where SCF approaches MEX as n_max grows), and
     SCF in the Clutton-Brock basis (Plummer zeroth term) at l_max = 6.  The
     overlap of the log10(eps) histograms of SCF and MEX at the same l_max (6
     and 10) measures that approach."""
