@@ -873,7 +873,7 @@ def run_gemm(args):
 
 
 def run_sweep(args):
-    """Shape sweeps of the paper's scaling study (Sec. 5: time against N,
+    """Shape sweeps of the paper's scaling study (Sec. 3.4, Fig. 5: time against N,
     l_max and n_max): SCF (coefficients + field) and MEX timed separately,
     mixed precision, on the flattened Hernquist model of the headline
     workload (the first N particles of one 2^24 realisation).  Each point is
