@@ -272,7 +272,7 @@ __device__ __forceinline__ void scan_rows(R (&v)[kMexNC], R* buf, R* total, int 
 // level group 4 (16 warps hide the gather latency); the multi-group kernels
 // and FP64 need more registers (FP64 pass 2 at 4 blocks spilled ~1 KB)
 template <typename R, int NG>
-constexpr int mex_pass1_blocks() { return sizeof(R) == 4 ? (NG == 1 ? 4 : 2) : 1; }
+constexpr int mex_pass1_blocks() { return sizeof(R) == 4 ? (NG == 1 ? 4 : 3) : 1; }
 template <typename R, int NG>
 constexpr int mex_pass2_blocks() { return sizeof(R) == 4 ? (NG == 1 ? 4 : 2) : (NG == 1 ? 2 : 1); }
 
