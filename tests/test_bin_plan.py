@@ -1,0 +1,77 @@
+"""Host-side check of the per-warp-bin plans of the SCF coefficient pass: for
+every level bound the plan assigns each harmonic column (l, c), c < 2l+1,
+to exactly one bin slot, no bin holds more than its column capacity or four
+level segments, and the finalize's column -> (bin, slot) map inverts the
+plan.  The plans are compile-time C++; a small host program prints them."""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(ROOT, "paper_1406_4254_gb300", "csrc")
+
+PROGRAM = r"""
+#include "etics_scf_bins.cuh"
+#include <cstdio>
+template <int LM> void show() {
+    constexpr auto p = etics::BinConst<LM>::plan;
+    constexpr auto ix = etics::make_bin_index<LM>();
+    printf("LM %d %d %d\n", LM, p.nbins, etics::kBinCap);
+    for (int b = 0; b < p.nbins; ++b) {
+        printf("B %d %d", b, p.bin[b].nseg);
+        for (int s = 0; s < p.bin[b].nseg; ++s)
+            printf(" %d %d %d", p.bin[b].seg[s].l, p.bin[b].seg[s].c0, p.bin[b].seg[s].n);
+        printf("\n");
+    }
+    for (int j = 0; j < (LM + 1) * (LM + 1); ++j) printf("I %d %d %d\n", j, ix.bin[j], ix.slot[j]);
+}
+int main() { show<2>(); show<4>(); show<6>(); show<8>(); return 0; }
+"""
+
+
+def _plans(tmp_path):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    src = tmp_path / "plan.cu"
+    exe = tmp_path / "plan"
+    src.write_text(PROGRAM)
+    r = subprocess.run([nvcc, "-std=c++17", "-I", CSRC, "-I", os.path.join(ROOT, "include"),
+                        "-o", str(exe), str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-2000:]
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    plans, cur = {}, None
+    for line in out.splitlines():
+        f = line.split()
+        if f[0] == "LM":
+            cur = {"lm": int(f[1]), "nbins": int(f[2]), "cap": int(f[3]), "bins": [], "index": {}}
+            plans[cur["lm"]] = cur
+        elif f[0] == "B":
+            v = list(map(int, f[3:]))
+            cur["bins"].append([tuple(v[i:i + 3]) for i in range(0, len(v), 3)])
+        else:
+            cur["index"][int(f[1])] = (int(f[2]), int(f[3]))
+    return plans
+
+
+def test_bin_plans_cover_every_column_once(tmp_path):
+    for lm, p in _plans(tmp_path).items():
+        assert len(p["bins"]) == p["nbins"]
+        seen = {}
+        for b, segs in enumerate(p["bins"]):
+            assert 1 <= len(segs) <= 4, (lm, b)
+            assert sum(n for _, _, n in segs) <= p["cap"], (lm, b)
+            off = 0
+            for l, c0, n in segs:
+                assert 0 <= l <= lm and n >= 1 and 0 <= c0 and c0 + n <= 2 * l + 1, (lm, b)
+                for c in range(c0, c0 + n):
+                    j = l * l + c
+                    assert j not in seen, (lm, j)
+                    seen[j] = (b, off + c - c0)
+                off += n
+        assert sorted(seen) == list(range((lm + 1) ** 2)), lm
+        # the finalize's map is the inverse of the plan
+        assert seen == p["index"], lm
