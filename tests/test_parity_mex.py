@@ -241,3 +241,18 @@ def test_full_size_bench_config(l_max):
     o = etics.mex_field(device_particles(pm, "mixed"), l_max).cpu().numpy()
     etics.check_error()
     assert_field_close(o, acc_ref, pot_ref, "mixed", f"mex 2^20 l={l_max}")
+
+
+def test_workspace_by_l_max():
+    """The MEX workspace holds 49 components per side up to l_max = 6 and
+    (l_max + 1)^2 above; l_max beyond the compiled limit has no workspace and
+    the call is refused."""
+    n = 100000
+    sizes = [etics.workspace_bytes(n, 0, l, etics.MEX, etics.MIXED) for l in range(11)]
+    assert all(s > 0 for s in sizes)
+    assert len(set(sizes[:7])) == 1                     # l_max <= 6: one layout
+    assert all(b > a for a, b in zip(sizes[6:], sizes[7:]))
+    assert etics.workspace_bytes(n, 0, 11, etics.MEX, etics.MIXED) == 0
+    d = device_particles(hernquist(1000, seed=41), "mixed")
+    with pytest.raises(etics.EticsError):
+        etics.mex_field(d, 11)
