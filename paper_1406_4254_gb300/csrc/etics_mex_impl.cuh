@@ -300,10 +300,14 @@ mex_pass1_kernel(const Vec4<R>* __restrict__ posm, const uint32_t* __restrict__ 
         const int i = tid + j * kMexThreads;
         Vec4<R> v = mk4<R>(R(0), R(0), R(0), R(0));
         if (i < nt) {
-            v = ld4(posm + idx[j]);
-            if (!finite4(v.x, v.y, v.z, v.w)) {
-                report(err, ETICS_ERR_NONFINITE);
-                v = mk4<R>(R(0), R(0), R(0), R(0));
+            // an index >= N can only come from a sort whose lookback timed
+            // out (already reported): it gathers a massless particle at 0
+            if ((int64_t)idx[j] < N) {
+                v = ld4(posm + idx[j]);
+                if (!finite4(v.x, v.y, v.z, v.w)) {
+                    report(err, ETICS_ERR_NONFINITE);
+                    v = mk4<R>(R(0), R(0), R(0), R(0));
+                }
             }
             st4(sorted + base + i, v);
         }
@@ -497,7 +501,8 @@ __device__ __forceinline__ void mex_pass2_group(const Vec4<R>* s_pt, Vec4<R>* s_
             continue;
         }
         const int64_t i = base + (int64_t)tid * kMexP + k;
-        if (i < N) {
+        // perm[i] >= N only after a timed-out sort (reported): no store
+        if (i < N && (int64_t)perm[i] < N) {
             const R potv = (out_mask & ETICS_OUT_POT) ? -pot * s1 : R(0);
             const R fx = ACC ? ax * s2 : R(0);
             const R fy = ACC ? ay * s2 : R(0);

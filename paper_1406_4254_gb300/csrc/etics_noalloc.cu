@@ -46,13 +46,15 @@ extern "C" int etics_scf_coeffs_noalloc(const void* posm, int64_t N, int n_max, 
         return ETICS_ERR_ARG;
     if (n_max < 0 || l_max < 0) return ETICS_ERR_ARG;
     if (n_max > ETICS_NMAX_LIMIT || l_max > ETICS_LMAX_LIMIT) return ETICS_ERR_UNSUPPORTED;
-    const size_t need = etics_workspace_bytes(N, n_max, l_max, ETICS_SCF, precision);
-    if (need == 0) return ETICS_ERR_ARG;
-    // the fixed array is too small for this expansion on this device
-    if (need > (size_t)ETICS_STATIC_SCRATCH_BYTES) return ETICS_ERR_WORKSPACE;
+    // the device lookups first, so that a failing CUDA call reads as
+    // ETICS_ERR_CUDA and not as a bad argument
     void* scratch = nullptr;
     const int rc = scratch_address(&scratch);
     if (rc) return rc;
+    const size_t need = etics_workspace_bytes(N, n_max, l_max, ETICS_SCF, precision);
+    if (need == 0) return ETICS_ERR_CUDA;   // the arguments were checked above
+    // the fixed array is too small for this expansion on this device
+    if (need > (size_t)ETICS_STATIC_SCRATCH_BYTES) return ETICS_ERR_WORKSPACE;
     // The partial sums are written in full by every call before they are
     // read, so nothing in the array has to start at zero.
     return etics_scf_coeffs(posm, N, n_max, l_max, precision, coeffs, scratch,

@@ -25,7 +25,7 @@ constexpr int kMatchDigits = 8;               // rank with match_any up to this 
 constexpr uint32_t kCountMask = (1u << 30) - 1;
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagInc = 2u << 30;
-constexpr int kSpinLimit = 1 << 22;
+constexpr int64_t kSpinLimit = int64_t(1) << 22;   // default bound of a lookback wait
 
 int sort_tiles(int64_t N) { return (int)((N + kSortTile - 1) / kSortTile); }
 
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(kSortThreads, 2)
 onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                 uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
                 const uint32_t* __restrict__ hist, uint32_t* status, uint32_t* counter, int shift,
-                int64_t N, unsigned* err) {
+                int64_t N, int64_t spin_limit, unsigned* err) {
     __shared__ uint32_t s_keys[kSortTile];
     __shared__ uint32_t s_vals[kSortTile];
     __shared__ uint32_t s_whist[kSortThreads / 32][256];
@@ -297,11 +297,16 @@ onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
     // decoupled lookback over earlier tiles for this digit: a window of
     // predecessors is read at once; flags become bit masks; counts are summed
     // up to the first inclusive prefix, or up to the first predecessor that
-    // has not published (then that one word is polled before the next window)
+    // has not published (then that one word is polled before the next window).
+    // The poll gives up after spin_limit tries: the error word records
+    // ETICS_ERR_TIMEOUT and the tile goes on with the partial prefix (at most
+    // the true one), so its output positions stay below N; keys that no
+    // longer match the histogram (a later pass of a timed-out sort) can
+    // compute a position >= N, and such a store is skipped below.
     uint32_t excl = 0;
     if (lookback) {
         const uint32_t* p = st - 256;   // tile - 1
-        int spins = 0;
+        int64_t spins = 0;
         for (;;) {
             uint32_t w[kLookbackWindow];
 #pragma unroll
@@ -326,7 +331,7 @@ onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
             if (used < kLookbackWindow) {
                 bool timed_out = false;
                 while ((ld_volatile(p) >> 30) == 0u) {
-                    if (++spins > kSpinLimit) { timed_out = true; break; }
+                    if (++spins > spin_limit) { timed_out = true; break; }
                     __nanosleep(32);
                 }
                 if (timed_out) { report(err, ETICS_ERR_TIMEOUT); break; }
@@ -345,16 +350,24 @@ onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
             const uint32_t kk = s_keys[i];
             const uint32_t dd = (kk >> shift) & 255u;
             const uint32_t pos = s_gbase[dd] + (uint32_t)i - s_dexcl[dd];
-            keys_out[pos] = kk;
-            vals_out[pos] = s_vals[i];
+            if (pos < N) {
+                keys_out[pos] = kk;
+                vals_out[pos] = s_vals[i];
+            } else {
+                report(err, ETICS_ERR_TIMEOUT);
+            }
         }
     } else {
         for (int i = tid; i < nvalid; i += kSortThreads) {
             const uint32_t kk = s_keys[i];
             const uint32_t dd = (kk >> shift) & 255u;
             const uint32_t pos = s_gbase[dd] + (uint32_t)i - s_dexcl[dd];
-            keys_out[pos] = kk;
-            vals_out[pos] = s_vals[i];
+            if (pos < N) {
+                keys_out[pos] = kk;
+                vals_out[pos] = s_vals[i];
+            } else {
+                report(err, ETICS_ERR_TIMEOUT);
+            }
         }
     }
 }
@@ -364,8 +377,10 @@ onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
 // the run members only.  The radix passes are stable and began from index
 // order, so a run's members arrive in index order: a stable sort by the low
 // word alone gives the (low word, index) order.
+// An index >= N (only after a timed-out sort) reads nothing and sorts last.
 template <typename R>
-__device__ __forceinline__ uint32_t r2_low(const Vec4<R>* posm, uint32_t i) {
+__device__ __forceinline__ uint32_t r2_low(const Vec4<R>* posm, uint32_t i, int64_t N) {
+    if ((int64_t)i >= N) return 0xffffffffu;
     const Vec4<R> v = ld4(posm + i);
     if (!finite4(v.x, v.y, v.z, v.w)) return 0xffffffffu;
     return (uint32_t)(uint64_t)__double_as_longlong(r2_fp64((double)v.x, (double)v.y, (double)v.z));
@@ -378,11 +393,11 @@ constexpr int kFixLongMax = kFixTile / (kFixLocal + 1) + 1;   // long runs start
 
 // a run of at most kFixLocal members, by one thread (insertion sort)
 template <typename R>
-__device__ __forceinline__ void sort_run_local(const Vec4<R>* posm, uint32_t* val, int64_t s,
-                                               int len) {
+__device__ __forceinline__ void sort_run_local(const Vec4<R>* posm, int64_t N, uint32_t* val,
+                                               int64_t s, int len) {
     uint32_t lows[kFixLocal], ids[kFixLocal];
     for (int a = 0; a < len; ++a) ids[a] = val[s + a];
-    for (int a = 0; a < len; ++a) lows[a] = r2_low<R>(posm, ids[a]);
+    for (int a = 0; a < len; ++a) lows[a] = r2_low<R>(posm, ids[a], N);
     for (int a = 1; a < len; ++a) {
         const uint32_t va = ids[a], la = lows[a];
         int b = a - 1;
@@ -406,8 +421,8 @@ __device__ __forceinline__ void sort_run_local(const Vec4<R>* posm, uint32_t* va
 // order, each member ranked among equal digits of its warp (ballots) and of
 // the earlier warps of the chunk.
 template <typename R>
-__device__ void sort_run_block(const Vec4<R>* posm, uint32_t* val, uint32_t* tmp, int64_t s,
-                               int64_t len, uint32_t (*s_cnt)[256], uint32_t* s_off,
+__device__ void sort_run_block(const Vec4<R>* posm, int64_t N, uint32_t* val, uint32_t* tmp,
+                               int64_t s, int64_t len, uint32_t (*s_cnt)[256], uint32_t* s_off,
                                uint32_t* s_wsum) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NW = kFixThreads / 32;
@@ -418,7 +433,7 @@ __device__ void sort_run_block(const Vec4<R>* posm, uint32_t* val, uint32_t* tmp
         for (int w = 0; w < NW; ++w) s_cnt[w][tid] = 0u;
         __syncthreads();
         for (int64_t i = tid; i < len; i += kFixThreads)
-            atomicAdd(&s_cnt[0][(r2_low<R>(posm, src[s + i]) >> shift) & 255u], 1u);
+            atomicAdd(&s_cnt[0][(r2_low<R>(posm, src[s + i], N) >> shift) & 255u], 1u);
         __syncthreads();
         {
             // exclusive scan over the 256 digits (thread = digit)
@@ -441,7 +456,7 @@ __device__ void sort_run_block(const Vec4<R>* posm, uint32_t* val, uint32_t* tmp
             const int64_t i = c0 + tid;
             const bool valid = i < len;
             const uint32_t v = valid ? src[s + i] : 0u;
-            const uint32_t d = valid ? (r2_low<R>(posm, v) >> shift) & 255u : 256u;
+            const uint32_t d = valid ? (r2_low<R>(posm, v, N) >> shift) & 255u : 256u;
             const unsigned vb = __ballot_sync(0xffffffffu, valid);
             unsigned mask = valid ? vb : ~vb;
 #pragma unroll
@@ -481,7 +496,8 @@ __device__ void sort_run_block(const Vec4<R>* posm, uint32_t* val, uint32_t* tmp
 template <typename R>
 __global__ void __launch_bounds__(kFixThreads)
 tie_fixup_kernel(const uint32_t* __restrict__ key, const Vec4<R>* __restrict__ posm,
-                 uint32_t* __restrict__ val, uint32_t* __restrict__ tmp, int64_t N) {
+                 uint32_t* __restrict__ val, uint32_t* __restrict__ tmp, int64_t N,
+                 unsigned* err) {
     __shared__ uint32_t s_key[kFixTile + 2];
     __shared__ int s_runs[kFixTile / 2];
     __shared__ int s_nruns, s_nlong;
@@ -533,17 +549,25 @@ tie_fixup_kernel(const uint32_t* __restrict__ key, const Vec4<R>* __restrict__ p
         }
         const int64_t len = lo - s + 1;
         if (len <= kFixLocal) {
-            sort_run_local<R>(posm, val, s, (int)len);
+            sort_run_local<R>(posm, N, val, s, (int)len);
         } else {
-            const int slot = atomicAdd(&s_nlong, 1);   // < kFixLongMax: members do not overlap
-            s_long_s[slot] = s;
-            s_long_n[slot] = len;
+            // sorted keys: long runs starting here do not overlap, so there
+            // are fewer than kFixLongMax; unsorted keys (only after a
+            // timed-out radix pass) can claim more, and those runs stay as
+            // they are
+            const int slot = atomicAdd(&s_nlong, 1);
+            if (slot < kFixLongMax) {
+                s_long_s[slot] = s;
+                s_long_n[slot] = len;
+            } else {
+                report(err, ETICS_ERR_TIMEOUT);
+            }
         }
     }
     __syncthreads();   // s_key and s_runs are dead from here
-    const int nlong = s_nlong;
+    const int nlong = s_nlong < kFixLongMax ? s_nlong : kFixLongMax;
     for (int r = 0; r < nlong; ++r)
-        sort_run_block<R>(posm, val, tmp, s_long_s[r], s_long_n[r], s_cnt, s_off, s_wsum);
+        sort_run_block<R>(posm, N, val, tmp, s_long_s[r], s_long_n[r], s_cnt, s_off, s_wsum);
 }
 
 // ---------------------------------------------------------------------------
@@ -593,7 +617,7 @@ int radial_sort_impl(const void* posm, int64_t N, const SortBuffers& b, const La
         if (launch_pdl(onesweep_kernel, dim3(nst), dim3(kSortThreads), 0, ctx.stream, (const uint32_t*)kin,
                        vals_in, kout, vout, (const uint32_t*)(b.hist + pass * 256),
                        b.status + (size_t)pass * (nst + kStatusPad) * 256, b.counters + pass, 8 * pass,
-                       N, ctx.err))
+                       N, ctx.wait_limit > 0 ? ctx.wait_limit : kSpinLimit, ctx.err))
             return ETICS_ERR_CUDA;
         ++*ctx.launches;
         uint32_t* t = kin; kin = kout; kout = t;
@@ -603,8 +627,39 @@ int radial_sort_impl(const void* posm, int64_t N, const SortBuffers& b, const La
     const int fg = (int)((N + kFixTile - 1) / kFixTile);
     if (launch_pdl(tie_fixup_kernel<R>, dim3(fg), dim3(kFixThreads), 0, ctx.stream,
                    (const uint32_t*)b.keys_a, reinterpret_cast<const Vec4<R>*>(posm), b.vals_a,
-                   b.vals_b, N))
+                   b.vals_b, N, ctx.err))
         return ETICS_ERR_CUDA;
+    ++*ctx.launches;
+    return ETICS_OK;
+}
+
+// One radix pass made to time out: kTimeoutProbeN keys, all 0, so the pass
+// histogram has one digit; the tile counter starts at 1, so the single block
+// takes tile 1 and looks back at tile 0, which never runs and never
+// publishes.  The lookback gives up after `spins` polls, records
+// ETICS_ERR_TIMEOUT and writes its tile at positions [0, kSortTile), inside
+// the output buffers.
+static __global__ void timeout_probe_setup_kernel(uint32_t* hist, uint32_t* counters, uint32_t n) {
+    if (threadIdx.x == 0) {
+        hist[0] = n;
+        counters[0] = 1u;
+    }
+}
+
+int lookback_timeout_probe(void* ws, int64_t spins, const LaunchCtx& ctx) {
+    static_assert(kTimeoutProbeN == 2 * kSortTile, "the probe sorts two tiles");
+    const SortBuffers b = sort_buffers(ws, kTimeoutProbeN, nullptr);
+    if (cudaMemsetAsync(b.zero_base, 0, b.zero_bytes, ctx.stream) ||
+        cudaMemsetAsync(b.keys_a, 0, kTimeoutProbeN * sizeof(uint32_t), ctx.stream))
+        return ETICS_ERR_CUDA;
+    timeout_probe_setup_kernel<<<1, 32, 0, ctx.stream>>>(b.hist, b.counters,
+                                                         (uint32_t)kTimeoutProbeN);
+    if (cudaGetLastError()) return ETICS_ERR_CUDA;
+    ++*ctx.launches;
+    onesweep_kernel<<<1, kSortThreads, 0, ctx.stream>>>(b.keys_a, nullptr, b.keys_b, b.vals_b,
+                                                         b.hist, b.status, b.counters, 0,
+                                                         kTimeoutProbeN, spins, ctx.err);
+    if (cudaGetLastError()) return ETICS_ERR_CUDA;
     ++*ctx.launches;
     return ETICS_OK;
 }

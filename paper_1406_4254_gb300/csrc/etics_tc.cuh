@@ -26,6 +26,8 @@ constexpr int kStages = 2;
 constexpr int kTileElems = kM * kK;          // one operand tile (A or B: kN == kM)
 constexpr int kTmemCols = kN;                // FP32 accumulator: 128 lanes x 128 columns
 constexpr long long kSpinLimit = 1ll << 22;
+// second, longer bound of the final drain before tensor memory is freed
+constexpr long long kDrainLimit = 1ll << 26;
 
 // shared memory of one block (dynamic, 1024-byte aligned base)
 struct Smem {
@@ -82,8 +84,9 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 }
 
 // bounded wait for the completion of the phase with this parity
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (long long i = 0; i < kSpinLimit; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          long long limit = kSpinLimit) {
+    for (long long i = 0; i < limit; ++i) {
         if (mbar_try(bar, parity)) return true;
         if (i > 32) __nanosleep(64);
     }
@@ -239,9 +242,15 @@ gemm_kernel(const bf16* __restrict__ A, int64_t lda, const bf16* __restrict__ B,
     }
     ok = __syncthreads_and(ok);
     // the last commit covers every MMA issued before it; on failure this is
-    // still the (bounded) wait for the MMAs in flight before TMEM is freed
-    const bool drained = issued == 0 || mbar_wait(smem_u32(&sm.mbar[(issued - 1) & 1]),
-                                                   (uint32_t)(((issued - 1) >> 1) & 1));
+    // still the (bounded) wait for the MMAs in flight before TMEM is freed,
+    // tried once more with a much longer bound.  Should that run out as well,
+    // TMEM is freed with MMAs possibly still writing it: the error word says
+    // ETICS_ERR_TIMEOUT, and the host must treat that as fatal for the
+    // context (later tensor-memory users on the SM could see those writes).
+    const uint32_t last_bar = smem_u32(&sm.mbar[(issued - 1) & 1]);
+    const uint32_t last_par = (uint32_t)(((issued - 1) >> 1) & 1);
+    bool drained = issued == 0 || mbar_wait(last_bar, last_par);
+    if (!drained) drained = mbar_wait(last_bar, last_par, kDrainLimit);
     ok = __syncthreads_and(ok && drained && issued == nk);
     if (!ok && tid == 0) report(err, ETICS_ERR_TIMEOUT);
     tc_fence_after();
@@ -269,6 +278,31 @@ gemm_kernel(const bf16* __restrict__ A, int64_t lda, const bf16* __restrict__ B,
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+// A wait that runs out on purpose: tensor memory held, an mbarrier that
+// nothing arrives on, a bound of `limit` tries.  Nothing is issued to the
+// tensor cores, so freeing the columns afterwards is safe; the error word
+// receives ETICS_ERR_TIMEOUT (what the product kernel does when a wait gives
+// up).
+__global__ void __launch_bounds__(kThreads) wait_timeout_kernel(long long limit, unsigned* err) {
+    __shared__ unsigned long long bar;
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (warp == 0) tmem_alloc(smem_u32(&tmem_slot), 32);
+    if (tid == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    const bool ok = __syncthreads_and(mbar_wait(smem_u32(&bar), 0u, limit));
+    if (!ok && tid == 0) report(err, ETICS_ERR_TIMEOUT);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 32);
 }
 
 }  // namespace tc
