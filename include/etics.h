@@ -293,6 +293,57 @@ int etics_force_error(const void *a, const void *r, int64_t N, int precision, do
  * (ETICS_OK if no kernel reported a data error since the last call). */
 int etics_get_error(void *stream);
 
+/* ---- failure detection ---------------------------------------------------
+ * The paper has no counterpart; these exist so that the error path of the
+ * bounded device waits can be exercised without faulting or hanging a GPU.
+ *
+ * Bound, in polls, of the waits of the MEX radial sort's decoupled lookback
+ * (a tile waiting for an earlier tile to publish its digit counts) in later
+ * calls on any stream; 0 restores the default (2^22 polls of >= 32 ns).
+ * When a wait runs out, the error word records ETICS_ERR_TIMEOUT, the tile
+ * goes on with a partial prefix, and every later kernel of the call keeps its
+ * reads and writes inside the caller's buffers (an order entry >= N is
+ * skipped), so the call returns with undefined outputs instead of faulting.
+ * A negative bound is ETICS_ERR_ARG.  Process-wide, not thread-safe. */
+int etics_set_wait_limit(int64_t spins);
+
+/* Makes one bounded wait run out on purpose and returns like the library's
+ * own kernels do when that happens (ETICS_ERR_TIMEOUT in the error word, no
+ * fault, the context stays usable):
+ *   ETICS_WAIT_LOOKBACK: one radix pass over 8192 keys whose single block
+ *     waits for a predecessor tile that never publishes, giving up after
+ *     `spins` polls.  ws: device workspace of at least
+ *     etics_workspace_bytes(8192, 0, 0, ETICS_MEX, ETICS_MIXED) bytes
+ *     (its contents are overwritten); a smaller ws_bytes is
+ *     ETICS_ERR_WORKSPACE.
+ *   ETICS_WAIT_MBARRIER: a block that holds tensor memory waits `spins`
+ *     tries on an mbarrier nothing arrives on (the wait of the tcgen05
+ *     products of the MLP), then frees the tensor memory.  ws is unused.
+ * spins < 0 or an unknown `which` is ETICS_ERR_ARG.  Asynchronous on stream;
+ * read the outcome with etics_get_error(). */
+#define ETICS_WAIT_LOOKBACK 0
+#define ETICS_WAIT_MBARRIER 1
+int etics_test_wait_timeout(int which, int64_t spins, void *ws, size_t ws_bytes, void *stream);
+
+/* ---- measurement aid -------------------------------------------------------
+ * The arithmetic rates behind the roofline fractions of the benchmark (the
+ * paper compares single- and double-precision speed, Sec. 3.4; it has no
+ * such entry point).  Launches `blocks` blocks of 256 threads, each thread
+ * running `iters` rounds of 256 fused multiply-adds on 16 independent
+ * accumulator chains:
+ *   ETICS_PEAK_FFMA:  FP32 fmaf;
+ *   ETICS_PEAK_FFMA2: the paired FP32 FMA (two FMAs per instruction);
+ *   ETICS_PEAK_DFMA:  FP64 fma.
+ * sink: device float[blocks * 256], overwritten with one value per thread (so
+ * that the work cannot be elided).  *flops_host (host) receives the
+ * floating-point operations of the launch (2 per FMA); time the launch with
+ * events on `stream`.  Bad arguments are ETICS_ERR_ARG. */
+#define ETICS_PEAK_FFMA 0
+#define ETICS_PEAK_FFMA2 1
+#define ETICS_PEAK_DFMA 2
+int etics_fma_peak(int kind, int blocks, int64_t iters, float *sink, double *flops_host,
+                   void *stream);
+
 /* Static description of a status code. */
 const char *etics_strerror(int status);
 

@@ -19,6 +19,7 @@ int g_num_sms[kMaxDevices] = {};
 std::atomic<uint64_t> g_launches{0};
 void** g_events = nullptr;
 int g_n_events = 0;
+std::atomic<int64_t> g_wait_limit{0};
 
 int current_device_state(unsigned** err, int* num_sms) {
     int dev = 0;
@@ -55,6 +56,7 @@ int make_ctx(void* stream, CtxHolder& h) {
     h.ctx.launches = &h.launches;
     h.ctx.events = g_events;
     h.ctx.n_events = g_n_events;
+    h.ctx.wait_limit = g_wait_limit.load();
     return ETICS_OK;
 }
 
@@ -457,6 +459,40 @@ const char* etics_strerror(int status) {
 }
 
 uint64_t etics_launch_count(void) { return g_launches.load(); }
+
+int etics_set_wait_limit(int64_t spins) {
+    if (spins < 0) return ETICS_ERR_ARG;
+    g_wait_limit = spins;
+    return ETICS_OK;
+}
+
+int etics_test_wait_timeout(int which, int64_t spins, void* ws, size_t ws_bytes, void* stream) {
+    if (spins < 0) return ETICS_ERR_ARG;
+    if (which != ETICS_WAIT_LOOKBACK && which != ETICS_WAIT_MBARRIER) return ETICS_ERR_ARG;
+    if (which == ETICS_WAIT_LOOKBACK) {
+        if (!ws || !aligned(ws, 256)) return ETICS_ERR_ARG;
+        if (ws_bytes < etics_workspace_bytes(etics::kTimeoutProbeN, 0, 0, ETICS_MEX, ETICS_MIXED))
+            return ETICS_ERR_WORKSPACE;
+    }
+    CtxHolder h;
+    const int rc = make_ctx(stream, h);
+    if (rc) return rc;
+    return which == ETICS_WAIT_LOOKBACK ? etics::lookback_timeout_probe(ws, spins, h.ctx)
+                                        : etics::mbarrier_timeout_probe(spins, h.ctx);
+}
+
+int etics_fma_peak(int kind, int blocks, int64_t iters, float* sink, double* flops_host,
+                   void* stream) {
+    if (kind != ETICS_PEAK_FFMA && kind != ETICS_PEAK_FFMA2 && kind != ETICS_PEAK_DFMA)
+        return ETICS_ERR_ARG;
+    if (blocks < 1 || blocks > (1 << 20) || iters < 0 || !sink || !aligned(sink, 4) ||
+        !flops_host)
+        return ETICS_ERR_ARG;
+    CtxHolder h;
+    const int rc = make_ctx(stream, h);
+    if (rc) return rc;
+    return etics::fma_peak(kind, blocks, iters, sink, flops_host, h.ctx);
+}
 
 int etics_set_stage_events(void** events, int n_events) {
     if (n_events < 0 || (n_events > 0 && !events)) return ETICS_ERR_ARG;

@@ -87,6 +87,9 @@ struct BasisTables {
     // the GPU (Re/Im of r^l P_l^m e^{i m phi}):  K_lm = sqrt((2l+1)/(4 pi)
     // (l-m)!/(l+m)!), times sqrt2 for m > 0.  Indexed [l*(l+1)/2 + m], m >= 0.
     double knorm[(kLmaxLimit + 1) * (kLmaxLimit + 2) / 2];
+    // knorm / (l-m)!: the normalisation of the factorial-scaled harmonics
+    // (l-m)! Z_l^m that the coefficient passes evaluate (harm_level_exact)
+    double knorm_fact[(kLmaxLimit + 1) * (kLmaxLimit + 2) / 2];
     // MEX weights 4pi/(2l+1) K_lm^2 = (l-m)!/(l+m)! (times 2 for m > 0)
     float mexw_f[(kLmaxLimit + 1) * (kLmaxLimit + 2) / 2];
     double mexw_d[(kLmaxLimit + 1) * (kLmaxLimit + 2) / 2];
@@ -133,6 +136,9 @@ constexpr BasisTables make_tables() {
             const int idx = l * (l + 1) / 2 + m;
             double k2 = (2.0 * l + 1.0) / (4.0 * kPi) * ratio * (m > 0 ? 2.0 : 1.0);
             t.knorm[idx] = csqrt(k2);
+            double fact = 1.0;   // (l-m)!
+            for (int k = 2; k <= l - m; ++k) fact *= (double)k;
+            t.knorm_fact[idx] = t.knorm[idx] / fact;
             const double w = ratio * (m > 0 ? 2.0 : 1.0);
             t.mexw_d[idx] = w;
             t.mexw_f[idx] = (float)w;
@@ -274,6 +280,41 @@ __device__ __forceinline__ void harm_level(const R* C1, const R* S1, const R* C2
     }
 }
 
+// The same harmonics scaled by (L-m)!, for the coefficient passes:
+//   H_L^m = (L-m)! Z_L^m(u) on the unit sphere (|u| = 1 taken exactly),
+//   H_m^m     = (2m-1) (ux + i uy) H_{m-1}^{m-1}
+//   H_{m+1}^m = (2m+1) uz H_m^m
+//   H_L^m     = (2L-1) uz H_{L-1}^m - (L+m-1)(L-m-1) H_{L-2}^m.
+// Every recursion constant is an integer, exact in FP32.  With the ratios
+// (2L-1)/(L-m) and (L+m-1)/(L-m) rounded to FP32 (harm_level above) the
+// rounding of the constants leaks into lower harmonics and, through
+// uz Z_1^0, into a constant: a bias of about -2e-8 in P_l (l >= 3, m = 0)
+// with a non-zero mean over the sphere, which every particle adds
+// coherently to the coefficients c_{n,l,0}.  Here only the individual
+// roundings remain, and they average out.  The factor 1/(L-m)! goes into the
+// FP64 normalisation (knorm_fact).
+template <typename R, int L>
+__device__ __forceinline__ void harm_level_exact(const R* C1, const R* S1, const R* C2,
+                                                 const R* S2, R ux, R uy, R uz, R* C, R* S) {
+    if constexpr (L == 0) {
+        C[0] = R(1);
+        S[0] = R(0);
+    } else {
+        constexpr R d = R(2 * L - 1);
+        C[L] = d * (ux * C1[L - 1] - uy * S1[L - 1]);
+        S[L] = d * (ux * S1[L - 1] + uy * C1[L - 1]);
+        const R duz = d * uz;
+        C[L - 1] = duz * C1[L - 1];
+        S[L - 1] = (L - 1 == 0) ? R(0) : duz * S1[L - 1];
+#pragma unroll
+        for (int m = 0; m + 2 <= L; ++m) {
+            const R b = R((L + m - 1) * (L - m - 1));
+            C[m] = fma(duz, C1[m], -b * C2[m]);
+            S[m] = (m == 0) ? R(0) : fma(duz, S1[m], -b * S2[m]);
+        }
+    }
+}
+
 // gradient of C_L^m (gc) and S_L^m (gs) from level L-1 values (C1, S1; m <= L-1)
 template <typename R, int L>
 __device__ __forceinline__ void harm_grad(const R* C1, const R* S1, int m, R gc[3], R gs[3]) {
@@ -388,6 +429,7 @@ struct LaunchCtx {
     uint64_t* launches;   // host launch counter
     void** events;        // stage events (nullable)
     int n_events;
+    int64_t wait_limit;   // bound of the radix sort's lookback waits (0: default)
 };
 
 inline void stage_event(const LaunchCtx& ctx, int k) {

@@ -49,6 +49,18 @@ int radial_keys_impl(const void* posm, int64_t N, uint32_t* keys, const LaunchCt
 template <typename R>
 int radial_sort_impl(const void* posm, int64_t N, const SortBuffers& b, const LaunchCtx& ctx);
 
+// the bounded waits made to run out (etics_test_wait_timeout): one radix pass
+// over kTimeoutProbeN keys whose only block takes tile 1 while tile 0 never
+// publishes (etics_sort.cu); an mbarrier nothing arrives on, with tensor
+// memory held (etics_mlp.cu)
+constexpr int64_t kTimeoutProbeN = 8192;
+int lookback_timeout_probe(void* ws, int64_t spins, const LaunchCtx& ctx);
+int mbarrier_timeout_probe(int64_t spins, const LaunchCtx& ctx);
+
+// ---- arithmetic-rate microbenchmark (etics_peak.cu) ------------------------
+int fma_peak(int kind, int blocks, int64_t iters, float* sink, double* flops,
+             const LaunchCtx& ctx);
+
 // ---- MEX (etics_mex_f32.cu / etics_mex_f64.cu) ----------------------------
 size_t mex_workspace_f32(int64_t N, int l_max);
 size_t mex_workspace_f64(int64_t N, int l_max);

@@ -643,6 +643,13 @@ int mlp_adam(const etics_mlp_shape* s, float* params, const float* grads, float*
     return ETICS_OK;
 }
 
+int mbarrier_timeout_probe(int64_t spins, const LaunchCtx& ctx) {
+    tc::wait_timeout_kernel<<<1, tc::kThreads, 0, ctx.stream>>>((long long)spins, ctx.err);
+    if (cudaGetLastError() != cudaSuccess) return ETICS_ERR_CUDA;
+    ++*ctx.launches;
+    return ETICS_OK;
+}
+
 int mlp_to_bf16(const etics_mlp_shape* s, const float* params, uint16_t* pb, const LaunchCtx& ctx) {
     const int64_t n = mlp_layout(s, 1).nparam;
     mlp_to_bf16_kernel<<<grid_1d(n, ctx), 256, 0, ctx.stream>>>(params, n,

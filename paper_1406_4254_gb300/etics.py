@@ -23,6 +23,10 @@ SCF, MEX = 0, 1
 FP64, MIXED = 0, 1
 OUT_ACC, OUT_POT = 1, 2
 NMAX_LIMIT, LMAX_LIMIT, MEX_LMAX_LIMIT = 16, 14, 10
+ERR_ARG, ERR_CUDA, ERR_WORKSPACE, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
+STATIC_SCRATCH_BYTES = 4 << 20      # ETICS_STATIC_SCRATCH_BYTES
+WAIT_LOOKBACK, WAIT_MBARRIER = 0, 1
+TIMEOUT_PROBE_N = 8192              # keys of the lookback probe
 
 _STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA runtime error", -3: "workspace too small",
            -4: "non-finite input or FP32 overflow", -5: "inter-block wait timed out",
@@ -102,6 +106,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         lib.etics_strerror.restype = ctypes.c_char_p
         lib.etics_launch_count.restype = ctypes.c_uint64
         lib.etics_set_stage_events.argtypes = [ctypes.POINTER(ctypes.c_void_p), i32]
+        lib.etics_set_wait_limit.argtypes = [i64]
+        lib.etics_fma_peak.argtypes = [i32, i32, i64, vp, ctypes.POINTER(dbl), vp]
+        lib.etics_test_wait_timeout.argtypes = [i32, i64, vp, sz, vp]
         for name in ("etics_scf_coeffs", "etics_scf_field", "etics_mex_field",
                      "etics_radial_sort", "etics_radial_keys", "etics_leapfrog_step",
                      "etics_scf_coeffs_noalloc", "etics_scf_batch_plan", "etics_scf_batch",
@@ -109,7 +116,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
                      "etics_scf_coeffs_basis", "etics_scf_field_basis", "etics_mlp_loss_grad",
                      "etics_mlp_adam", "etics_mlp_to_bf16", "etics_coeff_stats",
                      "etics_coeff_features", "etics_coeff_advance", "etics_force_error",
-                     "etics_get_error",
+                     "etics_get_error", "etics_set_wait_limit", "etics_test_wait_timeout",
+                     "etics_fma_peak",
                      "etics_set_stage_events"):
             getattr(lib, name).restype = i32
         _lib = lib
@@ -562,6 +570,37 @@ def check_error(stream=None):
     rc = get_error(stream)
     if rc:
         raise EticsError(rc, "device")
+
+
+def set_wait_limit(spins: int) -> None:
+    """Bound (in polls) of the radial sort's lookback waits; 0 = default."""
+    _check(load().etics_set_wait_limit(int(spins)), "etics_set_wait_limit")
+
+
+def probe_wait_timeout(which: int, spins: int, ws: torch.Tensor | None = None,
+                      stream=None) -> None:
+    """Make one bounded device wait run out (WAIT_LOOKBACK or WAIT_MBARRIER);
+    the outcome is read with get_error()."""
+    wp, wb = 0, 0
+    if which == WAIT_LOOKBACK:
+        if ws is None:
+            ws = workspace(TIMEOUT_PROBE_N, 0, 0, MEX, MIXED)
+        wp, wb = _aligned_ptr(ws)
+    _check(load().etics_test_wait_timeout(int(which), int(spins), wp or None, wb,
+                                          _stream(stream)), "etics_test_wait_timeout")
+
+
+PEAK_FFMA, PEAK_FFMA2, PEAK_DFMA = 0, 1, 2
+
+
+def fma_peak(kind: int, blocks: int, iters: int, sink: torch.Tensor, stream=None) -> float:
+    """Launch the FMA-rate microbenchmark; returns the launch's flop count."""
+    if sink.dtype != torch.float32 or not sink.is_cuda or sink.numel() < blocks * 256:
+        raise ValueError("sink must be a float32 CUDA tensor of blocks * 256 elements")
+    flops = ctypes.c_double()
+    _check(load().etics_fma_peak(int(kind), int(blocks), int(iters), sink.data_ptr(),
+                                 ctypes.byref(flops), _stream(stream)), "etics_fma_peak")
+    return float(flops.value)
 
 
 def launch_count() -> int:
