@@ -81,6 +81,8 @@ def _load():
         lib.etics_ref_jnl_b.argtypes = [c_int, c_int, c_int]
         lib.etics_ref_jnl_b.restype = c_double
         lib.etics_ref_scf_coeffs_b.argtypes = [c_int, dp, dp, c_long, c_int, c_int, dp]
+        lib.etics_ref_scf_coeffs_bt.argtypes = [c_int, dp, dp, c_long, c_int, c_int, dp, c_int]
+        lib.etics_ref_mex_field_t.argtypes = [dp, dp, c_long, c_int, dp, dp, lp, c_int]
         lib.etics_ref_scf_field_b.argtypes = [c_int, dp, c_long, c_int, c_int, dp, dp, dp, c_int]
         _lib = lib
         return lib
@@ -130,13 +132,15 @@ def ylm(l_max: int, x: float, y: float, z: float) -> np.ndarray:
     return out
 
 
-def scf_coeffs(pos, mass, n_max: int, l_max: int, basis: int = HO) -> np.ndarray:
-    """SCF coefficients c[n, l*l+l+m] (Sec. 2.4 eq. 18), shape (n_max+1, (l_max+1)^2)."""
+def scf_coeffs(pos, mass, n_max: int, l_max: int, basis: int = HO,
+               nthreads: int = 0) -> np.ndarray:
+    """SCF coefficients c[n, l*l+l+m] (Sec. 2.4 eq. 18), shape (n_max+1, (l_max+1)^2);
+    nthreads <= 0 uses every online core (the result is the same for any count)."""
     p = _pos(pos)
     m = np.ascontiguousarray(mass, dtype=np.float64)
     out = np.zeros((n_max + 1, (l_max + 1) ** 2))
-    _check(_load().etics_ref_scf_coeffs_b(basis, _dp(p), _dp(m), len(p), n_max, l_max,
-                                          _dp(out)), "scf_coeffs")
+    _check(_load().etics_ref_scf_coeffs_bt(basis, _dp(p), _dp(m), len(p), n_max, l_max,
+                                           _dp(out), int(nthreads)), "scf_coeffs")
     return out
 
 
@@ -153,15 +157,17 @@ def scf_field(pos, n_max: int, l_max: int, coeffs, nthreads: int = 0, basis: int
     return acc, pot
 
 
-def mex_field(pos, mass, l_max: int):
-    """MEX acceleration, potential and the radial order (Sec. 2.4 eqs. 15-17)."""
+def mex_field(pos, mass, l_max: int, nthreads: int = 0):
+    """MEX acceleration, potential and the radial order (Sec. 2.4 eqs. 15-17);
+    nthreads <= 0 uses every online core (the result is the same for any count)."""
     p = _pos(pos)
     m = np.ascontiguousarray(mass, dtype=np.float64)
     acc = np.zeros((len(p), 3))
     pot = np.zeros(len(p))
     order = np.zeros(len(p), dtype=np.int64)
-    _check(_load().etics_ref_mex_field(_dp(p), _dp(m), len(p), l_max, _dp(acc), _dp(pot),
-                                       order.ctypes.data_as(ctypes.POINTER(ctypes.c_long))),
+    _check(_load().etics_ref_mex_field_t(_dp(p), _dp(m), len(p), l_max, _dp(acc), _dp(pot),
+                                         order.ctypes.data_as(ctypes.POINTER(ctypes.c_long)),
+                                         int(nthreads)),
            "mex_field")
     return acc, pot, order
 

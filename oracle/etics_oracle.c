@@ -289,36 +289,85 @@ static void parallel_points(point_fn fn, void *ctx, long n, int nthreads)
 /* SCF                                                                       */
 /* ------------------------------------------------------------------------ */
 
-int etics_ref_scf_coeffs_b(int basis, const double *pos, const double *mass, long n_part,
-                           int n_max, int l_max, double *coeffs)
+/* The sum over particles is split into fixed chunks of consecutive
+ * particles, each summed serially in particle order into its own partial
+ * array; the partial arrays are then added in chunk order.  The chunk length
+ * depends on N alone (4096 particles, or N/1024 rounded up when that is
+ * larger), so the result is the same whatever the number of threads that
+ * sum the chunks. */
+static long coeff_chunk(long n_part)
+{
+    long c = (n_part + 1023) / 1024;
+    return c > 4096 ? c : 4096;
+}
+
+typedef struct {
+    const double *pos, *mass;
+    long n_part, chunk;
+    int n_max, l_max, basis;
+    double *part;   /* [nchunks][(n_max+1) * nj] */
+} coef_ctx_t;
+
+static void coef_chunks(void *vctx, long cbegin, long cend)
+{
+    coef_ctx_t *c = (coef_ctx_t *)vctx;
+    int nj = (c->l_max + 1) * (c->l_max + 1);
+    size_t ncoef = (size_t)(c->n_max + 1) * nj;
+    double *Y = (double *)malloc(sizeof(double) * nj);
+    double phi[64];
+    for (long ch = cbegin; ch < cend; ++ch) {
+        double *acc = c->part + (size_t)ch * ncoef;
+        memset(acc, 0, sizeof(double) * ncoef);
+        long k1 = (ch + 1) * c->chunk < c->n_part ? (ch + 1) * c->chunk : c->n_part;
+        for (long k = ch * c->chunk; k < k1; ++k) {
+            sph_t s;
+            to_sph(c->pos[3 * k], c->pos[3 * k + 1], c->pos[3 * k + 2], &s);
+            ylm_all(c->l_max, &s, Y, NULL, NULL);
+            for (int l = 0; l <= c->l_max; ++l) {
+                radial_all_b(c->basis, c->n_max, l, s.r, phi, NULL);
+                for (int n = 0; n <= c->n_max; ++n)
+                    for (int m = -l; m <= l; ++m) {
+                        int j = l * l + l + m;
+                        acc[(size_t)n * nj + j] += c->mass[k] * phi[n] * Y[j];
+                    }
+            }
+        }
+    }
+    free(Y);
+}
+
+int etics_ref_scf_coeffs_bt(int basis, const double *pos, const double *mass, long n_part,
+                            int n_max, int l_max, double *coeffs, int nthreads)
 {
     if ((basis != 0 && basis != 1) || n_part < 0 || n_max < 0 || n_max > 60 || l_max < 0 ||
         l_max > 60 || (n_part > 0 && (!pos || !mass)) || !coeffs)
         return -1;
     int nj = (l_max + 1) * (l_max + 1);
-    memset(coeffs, 0, sizeof(double) * (size_t)(n_max + 1) * nj);
-    double *Y = (double *)malloc(sizeof(double) * nj);
-    double phi[64];
-    for (long k = 0; k < n_part; ++k) {
-        sph_t s;
-        to_sph(pos[3 * k], pos[3 * k + 1], pos[3 * k + 2], &s);
-        ylm_all(l_max, &s, Y, NULL, NULL);
-        for (int l = 0; l <= l_max; ++l) {
-            radial_all_b(basis, n_max, l, s.r, phi, NULL);
-            for (int n = 0; n <= n_max; ++n)
-                for (int m = -l; m <= l; ++m) {
-                    int j = l * l + l + m;
-                    coeffs[(size_t)n * nj + j] += mass[k] * phi[n] * Y[j];
-                }
-        }
+    size_t ncoef = (size_t)(n_max + 1) * nj;
+    memset(coeffs, 0, sizeof(double) * ncoef);
+    if (n_part > 0) {
+        long chunk = coeff_chunk(n_part);
+        long nchunks = (n_part + chunk - 1) / chunk;
+        double *part = (double *)malloc(sizeof(double) * ncoef * (size_t)nchunks);
+        if (!part) return -2;
+        coef_ctx_t ctx = {pos, mass, n_part, chunk, n_max, l_max, basis, part};
+        parallel_points(coef_chunks, &ctx, nchunks, nthreads);
+        for (long ch = 0; ch < nchunks; ++ch)
+            for (size_t e = 0; e < ncoef; ++e) coeffs[e] += part[(size_t)ch * ncoef + e];
+        free(part);
     }
     for (int n = 0; n <= n_max; ++n)
         for (int l = 0; l <= l_max; ++l) {
             double J = etics_ref_jnl_b(basis, n, l);
             for (int m = -l; m <= l; ++m) coeffs[(size_t)n * nj + l * l + l + m] /= J;
         }
-    free(Y);
     return 0;
+}
+
+int etics_ref_scf_coeffs_b(int basis, const double *pos, const double *mass, long n_part,
+                           int n_max, int l_max, double *coeffs)
+{
+    return etics_ref_scf_coeffs_bt(basis, pos, mass, n_part, n_max, l_max, coeffs, 0);
 }
 
 int etics_ref_scf_coeffs(const double *pos, const double *mass, long n_part,
@@ -411,16 +460,6 @@ int etics_ref_scf_field(const double *pos, long n_part, int n_max, int l_max,
 /* MEX                                                                       */
 /* ------------------------------------------------------------------------ */
 
-typedef struct { double r2; long idx; } key_t_;
-
-static int key_cmp(const void *a, const void *b)
-{
-    const key_t_ *x = (const key_t_ *)a, *y = (const key_t_ *)b;
-    if (x->r2 < y->r2) return -1;
-    if (x->r2 > y->r2) return 1;
-    return (x->idx < y->idx) ? -1 : (x->idx > y->idx);
-}
-
 /* MEX (Sec. 2.4 eqs. 15-17):
  *   Phi(r_i) = - sum_l 4pi/(2l+1) sum_m [q_lm(i) r_i^-(l+1) + p_lm(i) r_i^l] Y_lm(i)
  *   q_lm(i)  = sum_{j before i} m_j r_j^l      Y_lm(j)
@@ -431,9 +470,118 @@ static int key_cmp(const void *a, const void *b)
  * and p backward (a true suffix sum), each serially in sorted order.
  * A particle at the origin sorts first: its own moment r^-(l+1) Y is taken as
  * zero, and its field uses the p terms of l = 0 (potential) and l = 1
- * (gradient of r Y_1m) only; q terms are skipped at the origin. */
-int etics_ref_mex_field(const double *pos, const double *mass, long n_part,
-                        int l_max, double *acc, double *pot, long *order)
+ * (gradient of r Y_1m) only; q terms are skipped at the origin.
+ *
+ * Work order: the sorted list is taken in blocks, forward for q and then
+ * backward for p.  In each block the particles' own moments are evaluated
+ * (independent per particle, so over threads), the running sum is carried
+ * through the block serially in sorted order (each particle keeps the sum
+ * over the particles strictly before it, resp. after it), and the field
+ * terms are evaluated from those kept sums (again per particle, over
+ * threads).  Every sum is thus formed in exactly the serial order, and the
+ * result does not depend on the number of threads. */
+
+typedef struct { double r2; long idx; } key_t_;
+
+static int key_cmp(const void *a, const void *b)
+{
+    const key_t_ *x = (const key_t_ *)a, *y = (const key_t_ *)b;
+    if (x->r2 < y->r2) return -1;
+    if (x->r2 > y->r2) return 1;
+    return (x->idx < y->idx) ? -1 : (x->idx > y->idx);
+}
+
+#define MEX_BLOCK 65536
+
+typedef struct {
+    const double *pos, *mass;
+    const key_t_ *key;
+    int L, outer;      /* outer = 0: inner sums q (forward), 1: outer sums p */
+    long k0;           /* first sorted position of the block */
+    double *mom;       /* [block][nj]: own moments, then the exclusive sums */
+    double *gP, *gG;   /* potential and grad Phi, by particle index */
+} mex_ctx_t;
+
+/* own moment of each particle of the block: m r^l Y (inner) or
+ * m r^-(l+1) Y (outer; zero at the origin) */
+static void mex_moments_pts(void *vctx, long begin, long end)
+{
+    mex_ctx_t *c = (mex_ctx_t *)vctx;
+    int L = c->L, nj = (L + 1) * (L + 1);
+    double *Y = (double *)malloc(sizeof(double) * nj);
+    for (long b = begin; b < end; ++b) {
+        long i = c->key[c->k0 + b].idx;
+        double *mo = c->mom + (size_t)b * nj;
+        sph_t s;
+        to_sph(c->pos[3 * i], c->pos[3 * i + 1], c->pos[3 * i + 2], &s);
+        ylm_all(L, &s, Y, NULL, NULL);
+        for (int l = 0; l <= L; ++l) {
+            double w;
+            if (!c->outer) w = (l == 0) ? 1.0 : pow(s.r, (double)l);
+            else w = (s.r > 0.0) ? pow(s.r, -(l + 1.0)) : 0.0;
+            for (int m = -l; m <= l; ++m) {
+                int j = l * l + l + m;
+                mo[j] = c->mass[i] * w * Y[j];
+            }
+        }
+    }
+    free(Y);
+}
+
+/* field terms of each particle of the block from its exclusive sum */
+static void mex_field_pts(void *vctx, long begin, long end)
+{
+    mex_ctx_t *c = (mex_ctx_t *)vctx;
+    int L = c->L, nj = (L + 1) * (L + 1);
+    double *Y = (double *)malloc(sizeof(double) * nj);
+    double *Yt = (double *)malloc(sizeof(double) * nj);
+    double *Yp = (double *)malloc(sizeof(double) * nj);
+    for (long b = begin; b < end; ++b) {
+        long i = c->key[c->k0 + b].idx;
+        const double *qp = c->mom + (size_t)b * nj;   /* q (inner) or p (outer) */
+        sph_t s;
+        to_sph(c->pos[3 * i], c->pos[3 * i + 1], c->pos[3 * i + 2], &s);
+        ylm_all(L, &s, Y, Yt, Yp);
+        if (s.r > 0.0) {
+            double P = 0.0, dr = 0.0, dt = 0.0, dp = 0.0;
+            for (int l = 0; l <= L; ++l) {
+                double w = 4.0 * PI / (2.0 * l + 1.0);
+                double f, df;
+                if (!c->outer) {
+                    f = pow(s.r, -(l + 1.0));                 /* r^-(l+1) */
+                    df = -(l + 1.0) * pow(s.r, -(l + 2.0));
+                } else {
+                    f = (l == 0) ? 1.0 : pow(s.r, (double)l); /* r^l */
+                    df = (l == 0) ? 0.0 : l * pow(s.r, l - 1.0);
+                }
+                for (int m = -l; m <= l; ++m) {
+                    int j = l * l + l + m;
+                    P  += -w * qp[j] * f * Y[j];
+                    dr += -w * qp[j] * df * Y[j];
+                    dt += -w * qp[j] * f * Yt[j];
+                    dp += -w * qp[j] * f * Yp[j];
+                }
+            }
+            c->gP[i] += P;
+            for (int d = 0; d < 3; ++d)
+                c->gG[3 * i + d] += dr * s.er[d] + (dt / s.r) * s.et[d] + (dp / s.r) * s.ep[d];
+        } else if (c->outer) {
+            /* origin: Phi = -4pi p_00 Y_00; grad from l = 1 only */
+            c->gP[i] += -4.0 * PI * qp[0] * (1.0 / sqrt(4.0 * PI));
+            if (L >= 1)
+                for (int m = -1; m <= 1; ++m) {
+                    double gv[3];
+                    grad_rY1(m, gv);
+                    for (int d = 0; d < 3; ++d)
+                        c->gG[3 * i + d] += -(4.0 * PI / 3.0) * qp[2 + m] * gv[d];
+                }
+        }
+    }
+    free(Y); free(Yt); free(Yp);
+}
+
+int etics_ref_mex_field_t(const double *pos, const double *mass, long n_part,
+                          int l_max, double *acc, double *pot, long *order, int nthreads)
 {
     if (n_part < 0 || l_max < 0 || l_max > 80 ||
         (n_part > 0 && (!pos || !mass)))
@@ -449,94 +597,58 @@ int etics_ref_mex_field(const double *pos, const double *mass, long n_part,
     qsort(key, n_part, sizeof(key_t_), key_cmp);
     if (order) for (long k = 0; k < n_part; ++k) order[k] = key[k].idx;
 
-    double *q = (double *)calloc(nj, sizeof(double));
-    double *p = (double *)calloc(nj, sizeof(double));
-    double *Y = (double *)malloc(sizeof(double) * nj);
-    double *Yt = (double *)malloc(sizeof(double) * nj);
-    double *Yp = (double *)malloc(sizeof(double) * nj);
-    double *gP = (double *)calloc(n_part, sizeof(double));      /* potential  */
-    double *gG = (double *)calloc(3 * n_part, sizeof(double));  /* grad Phi   */
+    long blk = n_part < MEX_BLOCK ? n_part : MEX_BLOCK;
+    double *run = (double *)calloc(nj, sizeof(double));          /* q, then p */
+    double *mom = (double *)malloc(sizeof(double) * (size_t)blk * nj);
+    double *gP = (double *)calloc(n_part, sizeof(double));       /* potential  */
+    double *gG = (double *)calloc(3 * n_part, sizeof(double));   /* grad Phi   */
+    mex_ctx_t ctx = {pos, mass, key, L, 0, 0, mom, gP, gG};
 
-    /* forward sweep: inner (q) part of the field, then add own moment */
-    for (long k = 0; k < n_part; ++k) {
-        long i = key[k].idx;
-        sph_t s;
-        to_sph(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], &s);
-        ylm_all(L, &s, Y, Yt, Yp);
-        if (s.r > 0.0) {
-            double P = 0.0, dr = 0.0, dt = 0.0, dp = 0.0;
-            for (int l = 0; l <= L; ++l) {
-                double w = 4.0 * PI / (2.0 * l + 1.0);
-                double rm = pow(s.r, -(l + 1.0));          /* r^-(l+1) */
-                double drm = -(l + 1.0) * pow(s.r, -(l + 2.0));
-                for (int m = -l; m <= l; ++m) {
-                    int j = l * l + l + m;
-                    P  += -w * q[j] * rm * Y[j];
-                    dr += -w * q[j] * drm * Y[j];
-                    dt += -w * q[j] * rm * Yt[j];
-                    dp += -w * q[j] * rm * Yp[j];
-                }
+    /* forward: inner sums q over the particles before each one */
+    for (long k0 = 0; k0 < n_part; k0 += blk) {
+        long nb = (n_part - k0 < blk) ? n_part - k0 : blk;
+        ctx.outer = 0;
+        ctx.k0 = k0;
+        parallel_points(mex_moments_pts, &ctx, nb, nthreads);
+        for (long b = 0; b < nb; ++b)
+            for (int j = 0; j < nj; ++j) {
+                double own = mom[(size_t)b * nj + j];
+                mom[(size_t)b * nj + j] = run[j];
+                run[j] += own;
             }
-            gP[i] += P;
-            for (int d = 0; d < 3; ++d)
-                gG[3 * i + d] += dr * s.er[d] + (dt / s.r) * s.et[d] + (dp / s.r) * s.ep[d];
-        }
-        for (int l = 0; l <= L; ++l) {
-            double rl = (l == 0) ? 1.0 : pow(s.r, (double)l);
-            for (int m = -l; m <= l; ++m) {
-                int j = l * l + l + m;
-                q[j] += mass[i] * rl * Y[j];
-            }
-        }
+        parallel_points(mex_field_pts, &ctx, nb, nthreads);
     }
-    /* backward sweep: outer (p) part of the field, then add own moment */
-    for (long k = n_part - 1; k >= 0; --k) {
-        long i = key[k].idx;
-        sph_t s;
-        to_sph(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], &s);
-        ylm_all(L, &s, Y, Yt, Yp);
-        if (s.r > 0.0) {
-            double P = 0.0, dr = 0.0, dt = 0.0, dp = 0.0;
-            for (int l = 0; l <= L; ++l) {
-                double w = 4.0 * PI / (2.0 * l + 1.0);
-                double rl = (l == 0) ? 1.0 : pow(s.r, (double)l);
-                double drl = (l == 0) ? 0.0 : l * pow(s.r, l - 1.0);
-                for (int m = -l; m <= l; ++m) {
-                    int j = l * l + l + m;
-                    P  += -w * p[j] * rl * Y[j];
-                    dr += -w * p[j] * drl * Y[j];
-                    dt += -w * p[j] * rl * Yt[j];
-                    dp += -w * p[j] * rl * Yp[j];
-                }
+    /* backward: outer sums p over the particles after each one (a true
+     * suffix sum, from the outside in) */
+    for (int j = 0; j < nj; ++j) run[j] = 0.0;
+    for (long k1 = n_part; k1 > 0; k1 -= blk) {
+        long k0 = (k1 - blk > 0) ? k1 - blk : 0;
+        long nb = k1 - k0;
+        ctx.outer = 1;
+        ctx.k0 = k0;
+        parallel_points(mex_moments_pts, &ctx, nb, nthreads);
+        for (long b = nb - 1; b >= 0; --b) {
+            int origin = key[k0 + b].r2 == 0.0;
+            for (int j = 0; j < nj; ++j) {
+                double own = mom[(size_t)b * nj + j];
+                mom[(size_t)b * nj + j] = run[j];
+                if (!origin) run[j] += own;
             }
-            gP[i] += P;
-            for (int d = 0; d < 3; ++d)
-                gG[3 * i + d] += dr * s.er[d] + (dt / s.r) * s.et[d] + (dp / s.r) * s.ep[d];
-            for (int l = 0; l <= L; ++l) {
-                double rm = pow(s.r, -(l + 1.0));
-                for (int m = -l; m <= l; ++m) {
-                    int j = l * l + l + m;
-                    p[j] += mass[i] * rm * Y[j];
-                }
-            }
-        } else {
-            /* origin: Phi = -4pi p_00 Y_00; grad from l = 1 only */
-            gP[i] += -4.0 * PI * p[0] * (1.0 / sqrt(4.0 * PI));
-            if (L >= 1)
-                for (int m = -1; m <= 1; ++m) {
-                    double gv[3];
-                    grad_rY1(m, gv);
-                    for (int d = 0; d < 3; ++d)
-                        gG[3 * i + d] += -(4.0 * PI / 3.0) * p[2 + m] * gv[d];
-                }
         }
+        parallel_points(mex_field_pts, &ctx, nb, nthreads);
     }
     for (long i = 0; i < n_part; ++i) {
         if (pot) pot[i] = gP[i];
         if (acc) for (int d = 0; d < 3; ++d) acc[3 * i + d] = -gG[3 * i + d];
     }
-    free(key); free(q); free(p); free(Y); free(Yt); free(Yp); free(gP); free(gG);
+    free(key); free(run); free(mom); free(gP); free(gG);
     return 0;
+}
+
+int etics_ref_mex_field(const double *pos, const double *mass, long n_part,
+                        int l_max, double *acc, double *pot, long *order)
+{
+    return etics_ref_mex_field_t(pos, mass, n_part, l_max, acc, pot, order, 0);
 }
 
 /* ------------------------------------------------------------------------ */

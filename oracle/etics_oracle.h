@@ -44,7 +44,10 @@ int etics_ref_ylm(int l_max, double x, double y, double z, double *Y);
 
 /* SCF coefficients (Sec. 2.4 eq. 18, Sec. 3.3 step 1):
  *   c[n][j] = (1/J_nl) sum_k m_k phi_nl(r_k) Y_j(theta_k, phi_k)
- * summed serially in particle order. */
+ * summed in fixed chunks of consecutive particles (each serially in particle
+ * order; the chunk sums added in chunk order, the chunk length a function of
+ * N alone), on all online cores; the result does not depend on the number
+ * of threads. */
 int etics_ref_scf_coeffs(const double *pos, const double *mass, long n_part,
                          int n_max, int l_max, double *coeffs);
 
@@ -61,6 +64,11 @@ int etics_ref_scf_field(const double *pos, long n_part, int n_max, int l_max,
  * order (nullable) receives the sorted particle indices. */
 int etics_ref_mex_field(const double *pos, const double *mass, long n_part,
                         int l_max, double *acc, double *pot, long *order);
+/* The same with a thread count (<= 0: all online cores); the cumulative sums
+ * stay serial, the per-particle moments and field terms run over threads, and
+ * the result is bitwise the same for every thread count. */
+int etics_ref_mex_field_t(const double *pos, const double *mass, long n_part,
+                          int l_max, double *acc, double *pot, long *order, int nthreads);
 
 /* The same three SCF functions for a chosen radial basis (Sec. 2.5):
  * basis 0 = Hernquist-Ostriker (as above), basis 1 = Clutton-Brock (the
@@ -70,6 +78,10 @@ int etics_ref_phi_nl_b(int basis, int n, int l, double r, double *phi, double *d
 double etics_ref_jnl_b(int basis, int n, int l);
 int etics_ref_scf_coeffs_b(int basis, const double *pos, const double *mass, long n_part,
                            int n_max, int l_max, double *coeffs);
+/* ... with a thread count (<= 0: all online cores; the result is bitwise the
+ * same for every thread count). */
+int etics_ref_scf_coeffs_bt(int basis, const double *pos, const double *mass, long n_part,
+                            int n_max, int l_max, double *coeffs, int nthreads);
 int etics_ref_scf_field_b(int basis, const double *pos, long n_part, int n_max, int l_max,
                           const double *coeffs, double *acc, double *pot, int nthreads);
 

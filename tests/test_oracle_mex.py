@@ -204,3 +204,28 @@ def test_bar_sampler_quadrupole():
     u = pm[:, :3] / np.linalg.norm(pm[:, :3], axis=1)[:, None]
     q = np.mean(u[:, 0] ** 2 - u[:, 1] ** 2)
     assert q == pytest.approx(4 * 0.3 / 15, abs=4 * math.sqrt(0.2 / 60000))
+
+
+def test_mex_threaded_blocks_match_serial_and_shell_theorem():
+    """The oracle's MEX takes the sorted list in blocks of 65536 with the
+    per-particle work over threads: for several blocks and a ragged tail the
+    result is bitwise the same for any thread count, and at l_max = 0 it
+    equals the shell theorem counted independently here (numpy sort and
+    cumulative sums), so the running sums cross block boundaries intact."""
+    n = 2 * 65536 + 1001
+    pm = inputs.hernquist(n, seed=21)
+    pm[7, :3] = 0.0                        # a particle at the origin
+    x, m = pm[:, :3], pm[:, 3]
+    a1, p1, o1 = oracle.mex_field(x, m, 3, nthreads=1)
+    a4, p4, o4 = oracle.mex_field(x, m, 3, nthreads=4)
+    assert np.array_equal(a1, a4) and np.array_equal(p1, p4) and np.array_equal(o1, o4)
+    a0, p0, order = oracle.mex_field(x, m, 0)
+    r2 = (x[:, 0] * x[:, 0] + x[:, 1] * x[:, 1]) + x[:, 2] * x[:, 2]
+    assert np.array_equal(order, np.lexsort((np.arange(n), r2)))
+    r = np.sqrt(r2[order])
+    ms = m[order]
+    inner = np.concatenate([[0.0], np.cumsum(ms)[:-1]])           # mass strictly inside
+    w = np.where(r > 0, ms / np.where(r > 0, r, 1.0), 0.0)
+    outer = np.concatenate([np.cumsum(w[::-1])[::-1][1:], [0.0]])  # sum over j outside
+    pot = -(np.where(r > 0, inner / np.where(r > 0, r, 1.0), 0.0) + outer)
+    np.testing.assert_allclose(p0[order], pot, rtol=1e-11, atol=0)

@@ -259,3 +259,21 @@ def test_sharded_coefficients_sum_to_full():
     parts = sum(oracle.scf_coeffs(pm[a:b, :3], pm[a:b, 3], 6, 4)
                 for a, b in [(0, 300), (300, 620), (620, 900)])
     np.testing.assert_allclose(parts, full, rtol=1e-12, atol=1e-15)
+
+
+def test_threaded_coefficients_match_exact_sum_of_particle_terms():
+    """The coefficient sum runs in fixed particle chunks over threads: its
+    result is bitwise the same for any thread count, and equals the exactly
+    rounded sum (math.fsum) of the single-particle coefficients (Sec. 2.4
+    eq. 18 is a plain sum over particles) to rounding, so no chunk boundary
+    drops or repeats a particle."""
+    n = 9000 + 17                           # three chunks of 4096 and a ragged tail
+    pm = inputs.hernquist(n, seed=12, axes=(1.0, 0.8, 0.6))
+    c1 = oracle.scf_coeffs(pm[:, :3], pm[:, 3], 4, 2, nthreads=1)
+    for nt in (2, 3, 0):
+        assert np.array_equal(oracle.scf_coeffs(pm[:, :3], pm[:, 3], 4, 2, nthreads=nt), c1)
+    terms = np.stack([oracle.scf_coeffs(pm[k:k + 1, :3], pm[k:k + 1, 3], 4, 2, nthreads=1)
+                      for k in range(n)])
+    exact = np.array([[math.fsum(terms[:, i, j]) for j in range(terms.shape[2])]
+                      for i in range(terms.shape[1])])
+    np.testing.assert_allclose(c1, exact, rtol=1e-13, atol=1e-15 * np.max(np.abs(exact)))
