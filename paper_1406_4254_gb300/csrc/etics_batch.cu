@@ -261,7 +261,8 @@ __global__ void batch_finalize_kernel(const void* __restrict__ plan,
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) {
         const int am = m < 0 ? -m : m;
-        coeffs[warp] = s * c_tab.knorm[l * (l + 1) / 2 + am] * c_tab.inv_j[n][l] * geg_gamma(0, l, n);
+        coeffs[warp] = s * c_tab.knorm_fact[l * (l + 1) / 2 + am] * c_tab.inv_j[n][l] *
+                       geg_gamma(0, l, n);
     }
 }
 

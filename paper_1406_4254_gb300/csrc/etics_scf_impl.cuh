@@ -70,17 +70,19 @@ __host__ inline size_t scf_coeff_smem(int NR, int l_max, int T, int W, int G) {
     return bytes + (size_t)W * NR * 4 * sizeof(double);
 }
 
-// phase 1, angular half: write the unnormalised harmonics of level 0..l_max
-// for particle k into Ys[col][k] (compile-time recursion over the level).
+// phase 1, angular half: write the factorial-scaled harmonics (l-m)! Z_l^m
+// (harm_level_exact; the finalize applies knorm_fact) of level 0..l_max for
+// particle k into Ys[col][k] (compile-time recursion over the level).
 // PAD: levels padded to multiples of 4 columns (col_offset_c); otherwise the
-// dense layout, level l starting at column l*l.
+// dense layout, level l starting at column l*l.  uu is unused: the
+// harmonics are taken on the unit sphere.
 template <typename R, int L, int LMU, bool PAD = true>
 __device__ __forceinline__ void angular_levels(R (&C)[3][LMU + 1], R (&S)[3][LMU + 1], R ux, R uy,
                                                R uz, R uu, int l_max, R* Ys, int T, int k) {
     if constexpr (L <= LMU) {
         if (L > l_max) return;
         constexpr int s0 = L % 3, s1 = (L + 2) % 3, s2 = (L + 1) % 3;
-        harm_level<R, L>(C[s1], S[s1], C[s2], S[s2], ux, uy, uz, uu, C[s0], S[s0]);
+        harm_level_exact<R, L>(C[s1], S[s1], C[s2], S[s2], ux, uy, uz, C[s0], S[s0]);
         constexpr int co = PAD ? col_offset_c(L) : L * L;
         Ys[(size_t)(co + 0) * T + k] = C[s0][0];
 #pragma unroll
@@ -276,7 +278,7 @@ static __global__ void scf_finalize_kernel(const double* __restrict__ partial, i
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) {
         const int am = m < 0 ? -m : m;
-        coeffs[warp] = s * c_tab.knorm[l * (l + 1) / 2 + am] * inv_j_of(basis, n, l) *
+        coeffs[warp] = s * c_tab.knorm_fact[l * (l + 1) / 2 + am] * inv_j_of(basis, n, l) *
                        geg_gamma(basis, l, n);
     }
 }
@@ -336,17 +338,25 @@ struct FieldEval {
                     cn = cnew;
                 }
                 if constexpr (sizeof(R) == 4) {
+                    // a pair whose second column is the padding (the last,
+                    // odd column) runs as one scalar FMA
                     const float2 cc = make_float2(cn, cn), dd = make_float2(dn, dn);
 #pragma unroll
                     for (int q = 0; q < NQ; ++q) {
                         const V4 v = ld4(reinterpret_cast<const V4*>(row) + q);
-                        if (2 * q < NP) {
+                        if (4 * q + 1 < NC) {
                             A2[2 * q] = __ffma2_rn(make_float2(v.x, v.y), cc, A2[2 * q]);
                             if (ACC) B2[2 * q] = __ffma2_rn(make_float2(v.x, v.y), dd, B2[2 * q]);
+                        } else if (4 * q < NC) {
+                            A2[2 * q].x = fmaf(v.x, cn, A2[2 * q].x);
+                            if (ACC) B2[2 * q].x = fmaf(v.x, dn, B2[2 * q].x);
                         }
-                        if (2 * q + 1 < NP) {
+                        if (4 * q + 3 < NC) {
                             A2[2 * q + 1] = __ffma2_rn(make_float2(v.z, v.w), cc, A2[2 * q + 1]);
                             if (ACC) B2[2 * q + 1] = __ffma2_rn(make_float2(v.z, v.w), dd, B2[2 * q + 1]);
+                        } else if (4 * q + 2 < NC) {
+                            A2[2 * q + 1].x = fmaf(v.z, cn, A2[2 * q + 1].x);
+                            if (ACC) B2[2 * q + 1].x = fmaf(v.z, dn, B2[2 * q + 1].x);
                         }
                     }
                 } else {
