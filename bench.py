@@ -11,7 +11,8 @@ metric is particle-forces per second: 2N per step (N by each method).
 Prints ONE JSON line (rank 0).  ``--impl reference`` times the CPU oracle (the
 FP64 reference implementation written from the paper) on a bounded sample of
 the same workload instead.  Multi-GPU (torchrun): independent replicas, one
-per GPU (the methods are not sharded), weak scaling.
+per GPU (neither method is sharded across GPUs: each GPU runs the whole
+workload on its own particles), weak scaling.
 """
 from __future__ import annotations
 
@@ -41,7 +42,7 @@ def workload_name(n):
     return f"hernquist-1:0.8:0.6 N={n} SCF(n_max=10,l_max=6)+MEX(l_max=6)"
 
 
-# --- algorithmic work per particle (kept in sync with the design doc) ------------
+# --- algorithmic work per particle (the useful-work counts of each kernel) ---
 def scf_coeff_flops(n, l):
     # contraction 2(n+1)(l+1)^2 + Gegenbauer 3(n+1)(l+1) + angular 4(l+1)^2 + 30
     return 2 * (n + 1) * (l + 1) ** 2 + 3 * (n + 1) * (l + 1) + 4 * (l + 1) ** 2 + 30
@@ -91,6 +92,49 @@ def mex_bytes(fp64=False):
 def fp32_peak_tflops():
     """FP32 CUDA-core peak derived from unit counts and the maximum SM clock."""
     return 152 * 128 * 2 * 2070.0 * 1e6 / 1e12
+
+
+def measure_fma_peaks(dev, target_ms=5.0, reps=5, kinds=None):
+    """FP32 and FP64 FMA rates of this GPU, in TFLOP/s, from the library's
+    FMA-chain microbenchmark (etics_fma_peak): each kind is timed with CUDA
+    events on the launching stream, best of `reps` launches of about
+    `target_ms` each (a burst, as the step's kernels run).  'fp32' is the
+    better of plain and paired FP32 FMAs."""
+    import torch
+    from paper_1406_4254_gb300 import etics
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = sms * 4
+    sink = torch.empty(blocks * 256, dtype=torch.float32, device=dev)
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kinds = kinds or {"ffma": etics.PEAK_FFMA, "ffma2": etics.PEAK_FFMA2, "dfma": etics.PEAK_DFMA}
+    out = {}
+    for name, kind in kinds.items():
+        iters = 64
+        for _ in range(8):   # calibrate the trip count to about target_ms
+            e0.record(s)
+            etics.fma_peak(kind, blocks, iters, sink)
+            e1.record(s)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            if ms > 0.5 * target_ms:
+                break
+            iters = int(iters * min(64.0, target_ms / max(ms, 1e-3)))
+        iters = max(1, int(iters * target_ms / max(ms, 1e-3)))
+        best = 0.0
+        for _ in range(reps):
+            e0.record(s)
+            flops = etics.fma_peak(kind, blocks, iters, sink)
+            e1.record(s)
+            torch.cuda.synchronize()
+            best = max(best, flops / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+        out[name] = best
+    etics.check_error()
+    if "ffma" in out and "ffma2" in out:
+        out["fp32"] = max(out["ffma"], out["ffma2"])
+    if "dfma" in out:
+        out["fp64"] = out["dfma"]
+    return out
 
 
 MEX_L_LIMIT = 10   # compiled l_max limit of the MEX kernels (ETICS_MEX_LMAX_LIMIT)
@@ -261,6 +305,12 @@ def run_etics(args, rank, world):
         step_concurrent()
     torch.cuda.synchronize()
     etics.check_error()
+    # the FP32 / FP64 FMA rates of this GPU, measured now (the roofline's
+    # denominators for the arithmetic-bound kernels)
+    peak_clocks = Clocks(local)
+    peak_clocks.start()
+    peaks_meas = measure_fma_peaks(dev)
+    peaks_meas["clocks"] = peak_clocks.stop()
 
     clocks = Clocks(local)
     times, stage = [], {k: [] for k in ("coef_kernel", "finalize", "field_kernel", "mex_keys",
@@ -371,6 +421,7 @@ def run_etics(args, rank, world):
         result = {"ms": ms, "value": value, "stage": {k: statistics.mean(v) for k, v in stage.items()},
                   "launches": launches, "clocks": clk, "e2e_ms": e2e_ms, "serial_ms": serial_ms,
                   "f64": (statistics.mean(f64_scf), statistics.mean(f64_mex)),
+                  "peaks": peaks_meas,
                   "out_scf": out_scf, "out_mex": out_mex, "x": x}
     if dist:
         dist.barrier()
@@ -378,57 +429,86 @@ def run_etics(args, rank, world):
     return result
 
 
-def accuracy(x, out_scf, out_mex):
-    """eps~ of eq. 23 (single against double precision of the same method) of
-    the mixed path: the library's FP64 path at the same (FP32-rounded)
-    positions is the reference; the parity tests tie that path to the FP64
-    oracle to 1e-13."""
+def eps_stats(a, r):
+    """median / p99 / max of eq. 23's relative force error |a - r| / |r|."""
+    e = np.linalg.norm(a - r, axis=1) / np.linalg.norm(r, axis=1)
+    return {"median": float(np.median(e)), "p99": float(np.quantile(e, 0.99)),
+            "max": float(e.max()), "sample": int(len(e))}
+
+
+def accuracy(x, out_scf, out_mex, sample=65536, seed=0):
+    """eps~ of eq. 23 (Sec. 4.2) of the mixed path's forces:
+      * against the FP64 oracle at the same (FP32-rounded) positions: SCF
+        coefficients by the oracle from all N particles, its field on a
+        seeded sample of `sample` particles; MEX by the oracle over all N
+        particles (its field at a particle depends on every other), every
+        particle compared;
+      * against the library's FP64 GPU path at the same positions (every
+        particle), which the parity tests tie to the oracle.
+    The oracle runs on all host cores."""
+    import oracle
     from paper_1406_4254_gb300 import etics
     xr = x.double()
     c = etics.scf_coeffs(xr, N_MAX, L_MAX)
     a_scf = etics.scf_field(xr, c, N_MAX, L_MAX)
     a_mex = etics.mex_field(xr, L_MAX)
     etics.check_error()
-
-    def eps(a, r):
-        a = a.double().cpu().numpy()[:, :3]
-        r = r.cpu().numpy()[:, :3]
-        return np.linalg.norm(a - r, axis=1) / np.linalg.norm(r, axis=1)
-
-    def st(e):
-        return {"median": float(np.median(e)), "p99": float(np.quantile(e, 0.99)),
-                "max": float(e.max()), "sample": int(len(e))}
-    return {"reference": "FP64 GPU path at the same positions",
-            "scf": st(eps(out_scf, a_scf)), "mex": st(eps(out_mex, a_mex))}
+    pm = xr.cpu().numpy()
+    o_scf = out_scf.double().cpu().numpy()[:, :3]
+    o_mex = out_mex.double().cpu().numpy()[:, :3]
+    t0 = time.perf_counter()
+    c_or = oracle.scf_coeffs(pm[:, :3], pm[:, 3], N_MAX, L_MAX)
+    idx = np.sort(np.random.default_rng(seed).choice(len(pm), min(sample, len(pm)),
+                                                      replace=False))
+    a_or, _ = oracle.scf_field(pm[idx, :3], N_MAX, L_MAX, c_or)
+    t1 = time.perf_counter()
+    m_or, _, _ = oracle.mex_field(pm[:, :3], pm[:, 3], L_MAX)
+    t2 = time.perf_counter()
+    scf = eps_stats(o_scf[idx], a_or)
+    scf["what"] = (f"oracle coefficients from all {len(pm)} particles, field at "
+                   f"{len(idx)} sampled particles")
+    mex = eps_stats(o_mex, m_or)
+    mex["what"] = f"oracle over all {len(pm)} particles, every particle compared"
+    return {"vs_oracle": {"reference": "FP64 CPU oracle at the same positions",
+                          "scf": scf, "mex": mex,
+                          "oracle_seconds": {"scf": t1 - t0, "mex": t2 - t1},
+                          "oracle_threads": oracle.default_threads()},
+            "vs_fp64_gpu": {"reference": "the library's FP64 GPU path at the same positions",
+                            "scf": eps_stats(o_scf, a_scf.cpu().numpy()[:, :3]),
+                            "mex": eps_stats(o_mex, a_mex.cpu().numpy()[:, :3])}}
 
 
 def oracle_step_time(pm_sample, nthreads=0):
     """Wall time of one oracle SCF (coeffs + field) and one MEX calculation
-    (nthreads for the field pass, the oracle's one threaded part; 0 = all)."""
+    on `nthreads` host threads (0 = all): the SCF coefficient sum in fixed
+    particle chunks, the field loops per particle, MEX's moments and field
+    terms per particle between serial cumulative sums."""
     import oracle
     x, m = pm_sample[:, :3], pm_sample[:, 3]
     t0 = time.perf_counter()
-    c = oracle.scf_coeffs(x, m, N_MAX, L_MAX)
+    c = oracle.scf_coeffs(x, m, N_MAX, L_MAX, nthreads=nthreads)
     oracle.scf_field(x, N_MAX, L_MAX, c, nthreads=nthreads)
     t1 = time.perf_counter()
-    oracle.mex_field(x, m, L_MAX)
+    oracle.mex_field(x, m, L_MAX, nthreads=nthreads)
     t2 = time.perf_counter()
     return t1 - t0, t2 - t1
 
 
-def cpu_baseline(n_sample, repeats, seed=0):
+def cpu_baseline(n, n_single, seed=0):
+    """The oracle on the host cores: one full step of the workload itself
+    (all N particles) on all cores, and a sample of n_single particles on
+    one core (the paper quotes one-core CPU figures, Sec. 3.4)."""
     import oracle
     from paper_1406_4254_gb300 import inputs
-    pm = inputs.hernquist(n_sample, seed=seed, axes=(1.0, 0.8, 0.6))
-    ts = [oracle_step_time(pm) for _ in range(repeats)]
-    t = statistics.mean(a + b for a, b in ts)
-    # one core, for comparison with the paper's one-core CPU figure (Sec. 3.4)
-    t1 = sum(oracle_step_time(pm, nthreads=1))
-    return {"value": 2 * n_sample / t, "unit": UNIT, "cores": oracle.default_threads(),
+    pm = inputs.hernquist(n, seed=seed, axes=(1.0, 0.8, 0.6)).astype(np.float32).astype(np.float64)
+    ts, tm = oracle_step_time(pm)
+    t1 = sum(oracle_step_time(pm[:n_single], nthreads=1))
+    return {"value": 2 * n / (ts + tm), "unit": UNIT, "cores": oracle.default_threads(),
             "kind": "oracle",
-            "sample": (f"{n_sample} particles of the same model, {repeats} steps; SCF field pass "
-                       f"threaded over particles, SCF coefficient and MEX passes serial"),
-            "single_core": {"value": 2 * n_sample / t1, "unit": UNIT, "cores": 1}}
+            "sample": (f"one step over all {n} particles of the workload (SCF {ts:.2f} s, "
+                       f"MEX {tm:.2f} s) on all cores"),
+            "single_core": {"value": 2 * n_single / t1, "unit": UNIT, "cores": 1,
+                            "sample": f"{n_single} particles of the workload"}}
 
 
 def run_leapfrog(args):
@@ -436,7 +516,8 @@ def run_leapfrog(args):
     kick-drift-kick steps at dt = 0.01 (the paper's integrator, Secs. 3.4 and
     5.4), each step one CUDA-graph replay of etics_leapfrog_step.  Reports the
     energy drift |dE/E0| of the mixed and FP64 paths and, every 10th step, the
-    relative force error (eq. 23) of the mixed path against the library's
+    relative force error (eq. 23) of the mixed path against the FP64 oracle
+    and against the library's
     FP64 path at the same positions (coefficients from all particles, field
     on a 16384-particle sample)."""
     import torch
@@ -483,23 +564,29 @@ def run_leapfrog(args):
             torch.cuda.synchronize()
             times.append(t0.elapsed_time(t1))
             if label == "mixed" and step % check_every == 0 and not args.no_accuracy:
+                # eq. 23 against the FP64 oracle at the same positions:
+                # coefficients from all particles, field on a 16384 sample;
+                # and against the library's FP64 GPU path (same sample)
+                import oracle
                 xp = x.double()
+                pm_now = xp.cpu().numpy()
+                idx_np = np.sort(np.random.default_rng(step).choice(n, 16384, replace=False))
+                c_or = oracle.scf_coeffs(pm_now[:, :3], pm_now[:, 3], N_MAX, L_MAX)
+                a_or, _ = oracle.scf_field(pm_now[idx_np, :3], N_MAX, L_MAX, c_or)
+                idx = torch.tensor(idx_np, device=dev)
                 c = etics.scf_coeffs(xp, N_MAX, L_MAX)
-                idx = torch.tensor(np.random.default_rng(step).choice(n, 16384, replace=False),
-                                   device=dev)
                 a_ref = etics.scf_field(xp[idx].contiguous(), c, N_MAX, L_MAX)
                 a_ref = a_ref.cpu().numpy()[:, :3]
                 a = acc.double()[idx].cpu().numpy()[:, :3]
-                e = np.linalg.norm(a - a_ref, axis=1) / np.linalg.norm(a_ref, axis=1)
-                errs.append({"step": step, "median": float(np.median(e)),
-                             "p99": float(np.quantile(e, 0.99)), "max": float(e.max())})
+                errs.append({"step": step, "vs_oracle": eps_stats(a, a_or),
+                             "vs_fp64_gpu": eps_stats(a, a_ref)})
         etics.check_error()
         e1 = energy()
         ms = statistics.mean(times)
         res[label] = {"ms_per_step": ms, "particle_steps_per_s": n / (ms * 1e-3),
                       "energy_drift": abs(e1 / e0 - 1.0), "E0": e0, "E_end": e1}
         if errs:
-            res[label]["force_error_vs_fp64"] = errs
+            res[label]["force_error"] = errs
     return {"experiment": "leapfrog", "workload": f"plummer b=1 N={n} SCF(10,6) "
             f"{steps} KDK steps dt={dt}, graph-captured step", **res}
 
@@ -939,6 +1026,50 @@ def run_sweep(args):
             "fp32_peak_note": FP32_PEAK_NOTE, "N": sweep_n, "l_max": sweep_l, "n_max": sweep_nmax}
 
 
+def run_peaks(args):
+    """FP32 and FP64 FMA rates of the GPU (the roofline denominators of the
+    arithmetic-bound kernels), from etics_fma_peak: as a burst (best of 5
+    launches of ~5 ms, what a kernel timed inside a short step sees) and
+    sustained (back-to-back launches of ~50 ms for ~3 s, median), with the SM
+    clocks sampled during each.  Nothing about the GPU's clocks or power
+    settings is changed."""
+    import torch
+    from paper_1406_4254_gb300 import etics
+    dev = torch.device("cuda", 0)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    out = {"experiment": "peaks", "sms": sms, "derived_fp32_tflops": fp32_peak_tflops(),
+           "derived_note": FP32_PEAK_NOTE, "burst": {}, "sustained": {}}
+    clk = Clocks(0)
+    clk.start()
+    out["burst"] = measure_fma_peaks(dev)
+    out["burst"]["clocks"] = clk.stop()
+    blocks = sms * 4
+    sink = torch.empty(blocks * 256, dtype=torch.float32, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for name, kind in (("ffma", etics.PEAK_FFMA), ("ffma2", etics.PEAK_FFMA2),
+                       ("dfma", etics.PEAK_DFMA)):
+        # calibrate a ~50 ms launch
+        iters = 256
+        e0.record()
+        etics.fma_peak(kind, blocks, iters, sink)
+        e1.record()
+        torch.cuda.synchronize()
+        iters = max(1, int(iters * 50.0 / max(e0.elapsed_time(e1), 1e-3)))
+        clk = Clocks(0)
+        clk.start()
+        rates, t_end = [], time.perf_counter() + 3.0
+        while time.perf_counter() < t_end:
+            e0.record()
+            flops = etics.fma_peak(kind, blocks, iters, sink)
+            e1.record()
+            torch.cuda.synchronize()
+            rates.append(flops / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+        out["sustained"][name] = statistics.median(rates)
+        out["sustained"][name + "_clocks"] = clk.stop()
+    etics.check_error()
+    return out
+
+
 def emit(obj):
     print(json.dumps(obj), flush=True)
 
@@ -955,7 +1086,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=65536)
     ap.add_argument("--experiment", choices=["leapfrog", "batch", "surrogate", "accuracy", "gemm",
-                                             "sweep"],
+                                             "sweep", "peaks"],
                     default=None)
     ap.add_argument("--gemm-mnk", type=int, nargs=3, default=[16384, 4096, 4096])
     ap.add_argument("--acc-n", type=int, nargs="+", default=[1000, 10000, 100000, 1000000])
@@ -983,6 +1114,9 @@ def main():
     if args.experiment == "sweep":
         emit(run_sweep(args))
         return
+    if args.experiment == "peaks":
+        emit(run_peaks(args))
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     cfg = {"workload": workload_name(args.n), "N": args.n, "n_max": N_MAX, "l_max": L_MAX,
@@ -992,7 +1126,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        n_s = 16384
+        n_s = 65536
         from paper_1406_4254_gb300 import inputs
         pm = inputs.hernquist(n_s, seed=0, axes=(1.0, 0.8, 0.6))
         for _ in range(args.warmup):
@@ -1019,11 +1153,15 @@ def main():
     n = args.n
     st = res["stage"]
     # every timed kernel against the roofline that bounds it; the dominant one
-    # (largest share of the step) is the headline roofline
-    fp32_peak = fp32_peak_tflops()
+    # (largest share of the step) is the headline roofline.  The FP32 peak is
+    # the rate measured in this run (FMA-chain microbenchmark); the figure
+    # derived from unit counts and the maximum clock is kept beside it.
+    pk = res["peaks"]
+    fp32_peak = pk["fp32"]
+    fp32_derived = fp32_peak_tflops()
     traffic = kernel_traffic()
     kern = {
-        "scf_coeff_bins_kernel": ("alu", st["coef_kernel"], scf_coeff_flops(N_MAX, L_MAX)),
+        "scf_coeff_pairs_kernel": ("alu", st["coef_kernel"], scf_coeff_flops(N_MAX, L_MAX)),
         "scf_field_kernel": ("alu", st["field_kernel"], scf_field_flops(N_MAX, L_MAX)),
         "mex_pass2_kernel": ("alu", st["mex_pass2"], mex_flops(L_MAX)),
         "mex_sort (keys + 4 radix passes + ties)": ("hbm", st["mex_keys"] + st["mex_sort"],
@@ -1036,6 +1174,7 @@ def main():
             ach = work * n / (ms_k * 1e-3) / 1e12
             table[name] = {"bound": "alu", "ms": ms_k, "achieved": ach, "peak": fp32_peak,
                            "unit": "TFLOP/s", "frac": ach / fp32_peak,
+                           "frac_of_derived": ach / fp32_derived,
                            "work_per_particle": work, "work_unit": "flop"}
         else:
             ach = work * n / (ms_k * 1e-3) / 1e9
@@ -1050,13 +1189,25 @@ def main():
                                       else parts[0] + 4 * parts[1] + parts[2])
         else:
             table[name]["traffic"] = traffic.get(name)
+    # the SCF pass as a whole (coefficient kernel + finalize + field kernel)
+    scf_work = scf_coeff_flops(N_MAX, L_MAX) + scf_field_flops(N_MAX, L_MAX)
+    scf_ach = scf_work * n / (st["scf"] * 1e-3) / 1e12
+    scf_total = {"bound": "alu", "ms": st["scf"], "achieved": scf_ach, "peak": fp32_peak,
+                 "unit": "TFLOP/s", "frac": scf_ach / fp32_peak,
+                 "frac_of_derived": scf_ach / fp32_derived, "work_per_particle": scf_work,
+                 "work_unit": "flop"}
     dom = max(table, key=lambda k: table[k]["ms"])
     d = table[dom]
+    peak_note_alu = (f"of measured: FP32 FMA rate measured in this run by etics_fma_peak "
+                     f"(16 independent FMA chains per thread, best of 5 bursts of ~5 ms): "
+                     f"FFMA {pk['ffma']:.2f}, paired FFMA2 {pk['ffma2']:.2f} TFLOP/s; "
+                     f"derived {FP32_PEAK_NOTE} = {fp32_derived:.2f}")
     roof = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"],
             "unit": d["unit"], "frac": d["frac"], "traffic": d["traffic"],
-            "peak_note": (FP32_PEAK_NOTE + " (derived from unit counts; not in "
-                          "MEASURED_PEAKS.json)") if d["bound"] == "alu" else
-            f"hbm_gbs of MEASURED_PEAKS.json ({src})"}
+            "peak_note": peak_note_alu if d["bound"] == "alu" else
+            f"of {src}: hbm_gbs of MEASURED_PEAKS.json"}
+    if d["bound"] == "alu":
+        roof["frac_of_derived"] = d["frac_of_derived"]
     other = {k: {kk: (round(vv, 6) if isinstance(vv, float) else vv) for kk, vv in v.items()}
              for k, v in table.items()}
     out = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world,
@@ -1073,16 +1224,31 @@ def main():
                             "on one stream (K steps after the timed region)",
            "stages_ms": {k: round(v, 5) for k, v in st.items()},
            "kernels": other,
+           "scf_total": {k: (round(v, 6) if isinstance(v, float) else v)
+                         for k, v in scf_total.items()},
+           "fma_peaks_tflops": {k: (round(v, 3) if isinstance(v, float) else v)
+                                for k, v in pk.items()},
            "fp64_path": {"scf_ms": res["f64"][0], "mex_ms": res["f64"][1],
                          "value": 2 * n / ((res["f64"][0] + res["f64"][1]) * 1e-3),
                          "scf_particle_forces_per_s": n / (res["f64"][0] * 1e-3),
-                         "mex_particle_forces_per_s": n / (res["f64"][1] * 1e-3)},
+                         "mex_particle_forces_per_s": n / (res["f64"][1] * 1e-3),
+                         "scf_roofline": {
+                             "bound": "alu", "unit": "TFLOP/s",
+                             "achieved": scf_work * n / (res["f64"][0] * 1e-3) / 1e12,
+                             "peak": pk["fp64"],
+                             "frac": scf_work * n / (res["f64"][0] * 1e-3) / 1e12 / pk["fp64"],
+                             "peak_note": "of measured: FP64 FMA rate of etics_fma_peak in "
+                                          "this run"},
+                         "mixed_over_fp64": {"scf": res["f64"][0] / st["scf"],
+                                             "mex": res["f64"][1] / st["mex"]}},
            "mixed_per_method": {"scf_particle_forces_per_s": n / (st["scf"] * 1e-3),
                                 "mex_particle_forces_per_s": n / (st["mex"] * 1e-3)}}
     if not args.no_accuracy:
-        out["accuracy_eps_mixed_vs_fp64"] = accuracy(res["x"], res["out_scf"], res["out_mex"])
+        acc = accuracy(res["x"], res["out_scf"], res["out_mex"])
+        out["accuracy_eps_mixed_vs_oracle"] = acc["vs_oracle"]
+        out["accuracy_eps_mixed_vs_fp64_gpu"] = acc["vs_fp64_gpu"]
     if not args.no_cpu_baseline and world >= 1:
-        out["cpu_baseline"] = cpu_baseline(args.cpu_sample, 3)
+        out["cpu_baseline"] = cpu_baseline(n, args.cpu_sample)
     emit(out)
 
 

@@ -8,6 +8,10 @@ namespace etics {
 
 // ---- SCF (etics_scf_f32.cu / etics_scf_f64.cu) ----------------------------
 size_t scf_workspace_f32(int64_t N, int n_max, int l_max, int num_sms);
+// particle-pair coefficient pass at (10, 6) (etics_scf_pairs_f32.cu)
+size_t scf_pairs106_workspace_f32(int num_sms);
+int scf_coeffs_pairs106_f32(const void* posm, int64_t N, double* coeffs, void* ws,
+                            const LaunchCtx& ctx);
 // per-warp-bin coefficient pass at (14, 8) (etics_scf_bins_f32.cu)
 size_t scf_bins148_workspace_f32(int num_sms);
 int scf_coeffs_bins148_f32(const void* posm, int64_t N, double* coeffs, void* ws,

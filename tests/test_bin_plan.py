@@ -75,3 +75,63 @@ def test_bin_plans_cover_every_column_once(tmp_path):
         assert sorted(seen) == list(range((lm + 1) ** 2)), lm
         # the finalize's map is the inverse of the plan
         assert seen == p["index"], lm
+
+
+PAIR_PROGRAM = r"""
+#include "etics_scf_pairs.cuh"
+#include <cstdio>
+template <int LM, int CAP> void show() {
+    constexpr auto p = etics::make_pair_plan<LM, CAP>();
+    printf("LM %d %d %d\n", LM, CAP, p.nbins);
+    for (int b = 0; b < p.nbins; ++b) printf("B %d %d %d %d\n", b, p.bin[b].l, p.bin[b].c0, p.bin[b].nc);
+    for (int j = 0; j < (LM + 1) * (LM + 1); ++j) printf("I %d %d %d\n", j, p.bin_of[j], p.slot_of[j]);
+}
+int main() { show<6, 3>(); show<6, 4>(); show<8, 3>(); return 0; }
+"""
+
+
+def test_pair_plans_split_each_level_evenly_and_invert(tmp_path):
+    """The particle-pair coefficient pass: every bin is one level's run of at
+    most CAP consecutive columns, each level is split into ceil((2l+1)/CAP)
+    bins whose widths differ by at most one, bins are ordered by width
+    (widest first, so the threads beyond the tile sit in the lightest warps),
+    and the finalize's column -> (bin, slot) map inverts the plan."""
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    src, exe = tmp_path / "pairs.cu", tmp_path / "pairs"
+    src.write_text(PAIR_PROGRAM)
+    r = subprocess.run([nvcc, "-std=c++17", "--expt-relaxed-constexpr", "-I", CSRC, "-I",
+                        os.path.join(ROOT, "include"), "-o", str(exe), str(src)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-2000:]
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    plans, cur = [], None
+    for line in out.splitlines():
+        f = list(map(int, line.split()[1:]))
+        if line.startswith("LM"):
+            cur = {"lm": f[0], "cap": f[1], "nbins": f[2], "bins": [], "index": {}}
+            plans.append(cur)
+        elif line.startswith("B"):
+            cur["bins"].append(tuple(f[1:]))
+        else:
+            cur["index"][f[0]] = (f[1], f[2])
+    assert len(plans) == 3
+    for p in plans:
+        lm, cap = p["lm"], p["cap"]
+        assert len(p["bins"]) == p["nbins"] == sum(-(-(2 * l + 1) // cap) for l in range(lm + 1))
+        seen = {}
+        widths = {}
+        for b, (l, c0, nc) in enumerate(p["bins"]):
+            assert 0 <= l <= lm and 1 <= nc <= cap and 0 <= c0 and c0 + nc <= 2 * l + 1
+            widths.setdefault(l, []).append(nc)
+            for c in range(c0, c0 + nc):
+                j = l * l + c
+                assert j not in seen
+                seen[j] = (b, c - c0)
+        assert sorted(seen) == list(range((lm + 1) ** 2))
+        assert seen == p["index"]
+        for l, w in widths.items():
+            assert max(w) - min(w) <= 1 and sum(w) == 2 * l + 1, (lm, cap, l, w)
+        nc_order = [nc for _, _, nc in p["bins"]]
+        assert nc_order == sorted(nc_order, reverse=True)
