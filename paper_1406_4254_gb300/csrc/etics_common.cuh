@@ -197,6 +197,16 @@ constexpr BasisTables make_tables() {
 
 static __constant__ BasisTables c_tab = make_tables();
 
+// The same tables as a compile-time object, for recursion constants that have
+// to become instruction immediates: a paired FP32 instruction takes register
+// operands only, so a constant-memory value would need a load into registers
+// at every use when the registers are too few to keep it.
+constexpr BasisTables kTabCE = make_tables();
+template <int B, int L, int N>
+struct GegBsConst {
+    static constexpr float v = kTabCE.gbs_f[B][L][N];
+};
+
 // rescaled Gegenbauer recursion constant bs_n and scale gam_n of radial basis
 // B (0 Hernquist-Ostriker, 1 Clutton-Brock; see BasisTables)
 template <typename R, int B = 0> __device__ __forceinline__ R geg_bs(int l, int n) {

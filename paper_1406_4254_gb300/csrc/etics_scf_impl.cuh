@@ -427,6 +427,7 @@ scf_field_kernel(const Vec4<R>* __restrict__ posm, int64_t N, int n_max, int l_m
     R* cs = reinterpret_cast<R*>(smem_raw);
     const int ncols = col_total(l_max);
     const int nj = (l_max + 1) * (l_max + 1);
+    pdl_wait();   // the coefficients come from the previous kernel
     for (int e = threadIdx.x; e < (n_max + 1) * ncols; e += blockDim.x) {
         const int n = e / ncols;
         int c = e % ncols, l = 0;
@@ -599,22 +600,25 @@ inline int launch_field_lm(const void* posm, int64_t N, int n_max, int l_max,
     if (grid < 1) grid = 1;
     const Vec4<R>* pp = reinterpret_cast<const Vec4<R>*>(posm);
     Vec4<R>* op = reinterpret_cast<Vec4<R>*>(out);
+    // launched as a programmatic dependent of the coefficient finalize (or
+    // whatever precedes it): its launch overlaps the predecessor's tail
+    cudaError_t e;
     if (out_mask & ETICS_OUT_ACC) {
         auto k = scf_field_kernel<R, LM, true, NM1, B>;
         if (smem > 48 * 1024 &&
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
             return ETICS_ERR_CUDA;
-        k<<<grid, kFieldThreads, smem, ctx.stream>>>(pp, N, n_max, l_max, coeffs, op, out_mask,
-                                                     ctx.err);
+        e = launch_pdl(k, dim3(grid), dim3(kFieldThreads), smem, ctx.stream, pp, N, n_max, l_max,
+                       coeffs, op, out_mask, ctx.err);
     } else {
         auto k = scf_field_kernel<R, LM, false, NM1, B>;
         if (smem > 48 * 1024 &&
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))
             return ETICS_ERR_CUDA;
-        k<<<grid, kFieldThreads, smem, ctx.stream>>>(pp, N, n_max, l_max, coeffs, op, out_mask,
-                                                     ctx.err);
+        e = launch_pdl(k, dim3(grid), dim3(kFieldThreads), smem, ctx.stream, pp, N, n_max, l_max,
+                       coeffs, op, out_mask, ctx.err);
     }
-    if (cudaGetLastError() != cudaSuccess) return ETICS_ERR_CUDA;
+    if (e != cudaSuccess) return ETICS_ERR_CUDA;
     ++*ctx.launches;
     return ETICS_OK;
 }

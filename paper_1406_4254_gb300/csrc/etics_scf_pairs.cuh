@@ -31,6 +31,8 @@
 // that do no phase-1 work (threads beyond the tile).
 #pragma once
 
+#include <atomic>
+
 #include "etics_scf_impl.cuh"
 
 namespace etics {
@@ -119,6 +121,20 @@ __device__ __forceinline__ void pair_angular(float (&C)[3][LM + 1], float (&S)[3
     }
 }
 
+// recursion steps n = N..NR-1 of one particle pair: Ct_n = xi Ct_{n-1} -
+// bs_n Ct_{n-2}, then acc[n][c] += Ct_n y_c; bs_n an immediate
+template <int NR, int CAP, int NC, int L, int N>
+__device__ __forceinline__ void pair_steps(float2 (&acc)[NR][CAP], const float2 (&y)[NC],
+                                           float2 xi, float2 cm1, float2 cn) {
+    if constexpr (N < NR) {
+        constexpr float nb = -GegBsConst<0, L, N>::v;
+        const float2 cnew = __ffma2_rn(make_float2(nb, nb), cm1, __fmul2_rn(xi, cn));
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[N][c] = __ffma2_rn(cnew, y[c], acc[N][c]);
+        pair_steps<NR, CAP, NC, L, N + 1>(acc, y, xi, cn, cnew);
+    }
+}
+
 // phase 2 for bin B over one tile
 template <int NR, int LM, int CAP, int B>
 __device__ __forceinline__ void pair_bin_tile(float2 (&acc)[NR][CAP], const float* H,
@@ -137,19 +153,10 @@ __device__ __forceinline__ void pair_bin_tile(float2 (&acc)[NR][CAP], const floa
 #pragma unroll
         for (int c = 0; c < NC; ++c) acc[0][c] = __fadd2_rn(acc[0][c], y[c]);
         if constexpr (NR > 1) {
-            // Ct_1 = xi; Ct_n = xi Ct_{n-1} - bs_n Ct_{n-2}
-            float2 cm1 = make_float2(1.0f, 1.0f), cn = xi;
+            // Ct_0 = 1, Ct_1 = xi; Ct_n = xi Ct_{n-1} - bs_n Ct_{n-2}
 #pragma unroll
-            for (int c = 0; c < NC; ++c) acc[1][c] = __ffma2_rn(cn, y[c], acc[1][c]);
-#pragma unroll
-            for (int n = 2; n < NR; ++n) {
-                const float nb = -geg_bs<float, 0>(bd.l, n);
-                const float2 cnew = __ffma2_rn(make_float2(nb, nb), cm1, __fmul2_rn(xi, cn));
-                cm1 = cn;
-                cn = cnew;
-#pragma unroll
-                for (int c = 0; c < NC; ++c) acc[n][c] = __ffma2_rn(cn, y[c], acc[n][c]);
-            }
+            for (int c = 0; c < NC; ++c) acc[1][c] = __ffma2_rn(xi, y[c], acc[1][c]);
+            pair_steps<NR, CAP, NC, bd.l, 2>(acc, y, xi, make_float2(1.0f, 1.0f), xi);
         }
     }
 }
@@ -187,6 +194,7 @@ scf_coeff_pairs_kernel(ScfPairParams p) {
     auto Xb = [&](int b) { return buf0 + b * kBuf + (size_t)NCOL * kPairTile; };
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int e = tid; e < NOUT; e += TH) accd[e] = 0.0;
+    pdl_wait();   // the particles may come from the previous kernel (a drift)
 
     float2 acc[NR][CAP];
 #pragma unroll
@@ -194,19 +202,33 @@ scf_coeff_pairs_kernel(ScfPairParams p) {
 #pragma unroll
         for (int c = 0; c < CAP; ++c) acc[n][c] = make_float2(0.0f, 0.0f);
 
-    const int ncw = warp < NB ? c_pair_plan<LM, CAP>.bin[warp].nc : 0;   // this bin's columns
+    // Flush: every warp total of the NR x CAP accumulators (pair halves
+    // added, then a butterfly over the lanes) is kept by lane (index % 32),
+    // so that the FP64 additions into the block sums run as a few warp-wide
+    // instructions instead of one instruction per value (FP64 issue is slow
+    // on this GPU).  Columns beyond the bin's width hold zeros.
+    constexpr int kPerWarp = NR * CAP;
+    constexpr int kRounds = (kPerWarp + 31) / 32;
     auto flush = [&]() {
+        float mine[kRounds];
+#pragma unroll
+        for (int r = 0; r < kRounds; ++r) mine[r] = 0.0f;
 #pragma unroll
         for (int n = 0; n < NR; ++n)
 #pragma unroll
             for (int c = 0; c < CAP; ++c) {
-                if (c >= ncw) break;
                 float v = acc[n][c].x + acc[n][c].y;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (lane == 0) accd[(warp * NR + n) * CAP + c] += (double)v;
+                const int idx = n * CAP + c;
+                if (lane == (idx & 31)) mine[idx >> 5] = v;
                 acc[n][c] = make_float2(0.0f, 0.0f);
             }
+#pragma unroll
+        for (int r = 0; r < kRounds; ++r) {
+            const int idx = r * 32 + lane;
+            if (idx < kPerWarp) accd[warp * kPerWarp + idx] += (double)mine[r];
+        }
     };
     auto load = [&](int tile) -> float4 {
         const int64_t gi = (int64_t)tile * kPairTile + tid;
@@ -253,6 +275,7 @@ __global__ void scf_finalize_pairs_kernel(const double* __restrict__ partial, in
                                           double* __restrict__ coeffs) {
     constexpr int NJ = (LM + 1) * (LM + 1);
     constexpr int NOUT = PairConst<LM, CAP>::nbins * NR * CAP;
+    pdl_wait();
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= NR * NJ) return;
@@ -293,19 +316,27 @@ inline int scf_coeffs_pairs_launch(const void* posm, int64_t N, double* coeffs, 
     int nblocks = 0;
     if (ntiles > 0) {
         auto k = scf_coeff_pairs_kernel<NR, LM, CAP>;
-        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ||
-            cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100))
-            return ETICS_ERR_CUDA;
-        k<<<grid, TH, smem, ctx.stream>>>(p);
-        if (cudaGetLastError() != cudaSuccess) return ETICS_ERR_CUDA;
+        // the function attributes are set once per device (a host call per
+        // launch would sit between the caller's events and the kernel)
+        static std::atomic<uint64_t> attr_done{0};
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return ETICS_ERR_CUDA;
+        const uint64_t bit = uint64_t(1) << (dev & 63);
+        if (!(attr_done.load() & bit)) {
+            if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ||
+                cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100))
+                return ETICS_ERR_CUDA;
+            attr_done.fetch_or(bit);
+        }
+        if (launch_pdl(k, dim3(grid), dim3(TH), smem, ctx.stream, p)) return ETICS_ERR_CUDA;
         ++*ctx.launches;
         nblocks = grid;
     }
     stage_event(ctx, 1);
     const int nc = NR * (LM + 1) * (LM + 1);
-    scf_finalize_pairs_kernel<NR, LM, CAP><<<(nc * 32 + 255) / 256, 256, 0, ctx.stream>>>(
-        p.partial, nblocks, coeffs);
-    if (cudaGetLastError() != cudaSuccess) return ETICS_ERR_CUDA;
+    if (launch_pdl(scf_finalize_pairs_kernel<NR, LM, CAP>, dim3((nc * 32 + 255) / 256), dim3(256),
+                   0, ctx.stream, (const double*)p.partial, nblocks, coeffs))
+        return ETICS_ERR_CUDA;
     ++*ctx.launches;
     return ETICS_OK;
 }
