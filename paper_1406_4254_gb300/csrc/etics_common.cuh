@@ -413,7 +413,7 @@ __host__ __device__ __forceinline__ int col_total(int lmax) { return col_offset(
 // explicitly: the implicit trigger at block exit keeps waiting blocks from
 // holding SM slots that a concurrent stream could use.  pdl_wait() is a
 // no-op in a kernel launched the ordinary way.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { cudaGridDependencySynchronize(); }
 
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,

@@ -594,8 +594,11 @@ template <typename R, int LM, int NM1 = 0, int B = 0>
 inline int launch_field_lm(const void* posm, int64_t N, int n_max, int l_max,
                            const double* coeffs, void* out, int out_mask, const LaunchCtx& ctx) {
     const size_t smem = (size_t)(n_max + 1) * col_total(l_max) * sizeof(R);
+    // at most 4 blocks per SM (two resident at a time): each block builds the
+    // FP32 coefficient table once (FP64 multiplies, slow on this GPU) and then
+    // walks its particles; 8 per SM measured 5% slower at N = 2^20
     int64_t want = (N + kFieldThreads - 1) / kFieldThreads;
-    const int64_t cap = (int64_t)ctx.num_sms * 8;
+    const int64_t cap = (int64_t)ctx.num_sms * 4;
     int grid = (int)(want < cap ? want : cap);
     if (grid < 1) grid = 1;
     const Vec4<R>* pp = reinterpret_cast<const Vec4<R>*>(posm);

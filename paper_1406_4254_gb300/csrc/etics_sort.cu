@@ -119,9 +119,9 @@ keygen_kernel(const Vec4<R>* __restrict__ posm, int64_t N, uint32_t* __restrict_
                 hi = 0xffffffffu;
             }
             key[i] = hi;
+            // the histograms of digits 1 and 2 are counted by the radix
+            // passes 0 and 1 (their keys are in registers there anyway)
             atomicAdd(&sh[warp][hi & 255], 1u);
-            atomicAdd(&sh[warp][256 + ((hi >> 8) & 255)], 1u);
-            atomicAdd(&sh[warp][512 + ((hi >> 16) & 255)], 1u);
             // the top byte (sign + high exponent bits) takes very few values:
             // aggregate equal digits within the warp before the atomic
             const uint32_t d3 = hi >> 24;
@@ -132,6 +132,7 @@ keygen_kernel(const Vec4<R>* __restrict__ posm, int64_t N, uint32_t* __restrict_
     }
     __syncthreads();
     for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) {
+        if (i >= 256 && i < 768) continue;   // digits 1, 2: counted by the passes
         uint32_t t = 0;
         for (int w = 0; w < 8; ++w) t += sh[w][i];
         if (t) atomicAdd(&hist[i], t);
@@ -222,8 +223,8 @@ __device__ __forceinline__ void rank_in_warp(const uint32_t (&d)[kSortKpt], uint
 __global__ void __launch_bounds__(kSortThreads, 2)
 onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                 uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
-                const uint32_t* __restrict__ hist, uint32_t* status, uint32_t* counter, int shift,
-                int64_t N, int64_t spin_limit, unsigned* err) {
+                const uint32_t* hist, uint32_t* status, uint32_t* counter, int shift,
+                int64_t N, int64_t spin_limit, uint32_t* __restrict__ next_hist, unsigned* err) {
     __shared__ uint32_t s_keys[kSortTile];
     __shared__ uint32_t s_vals[kSortTile];
     __shared__ uint32_t s_whist[kSortThreads / 32][256];
@@ -231,12 +232,17 @@ onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
     __shared__ uint32_t s_gbase[256];
     __shared__ uint32_t s_scan[2][kSortThreads / 32];
     __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_next[256];   // this tile's histogram of the next digit
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int i = tid; i < (kSortThreads / 32) * 256; i += kSortThreads) (&s_whist[0][0])[i] = 0;
+    s_next[tid] = 0;
     pdl_wait();
     if (tid == 0) s_tile = atomicAdd(counter, 1u);
     const int dig = tid;
-    const uint32_t gcount = hist[dig];
+    // the histogram may have been completed by the kernel just before this
+    // one (a programmatic dependent launch): a coherent load after the wait,
+    // never the non-coherent read-only path
+    const uint32_t gcount = __ldcg(hist + dig);
     // digits present in this pass over all keys: few -> rank with match_any
     const int ndig = __syncthreads_count(gcount != 0u);
     const uint32_t tile = s_tile;
@@ -258,7 +264,16 @@ onesweep_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
     }
     if (ndig <= kMatchDigits) rank_in_warp<true>(d, rank, s_whist[warp], lane);
     else rank_in_warp<false>(d, rank, s_whist[warp], lane);
+    if (next_hist) {
+        // the next pass's digit of this tile's keys (the order of the keys
+        // does not matter for a histogram): added to the global histogram,
+        // which the next pass reads after this one has completed
+#pragma unroll
+        for (int s = 0; s < kSortKpt; ++s)
+            if (d[s] < 256u) atomicAdd(&s_next[(k[s] >> (shift + 8)) & 255u], 1u);
+    }
     __syncthreads();
+    if (next_hist && s_next[tid]) atomicAdd(&next_hist[tid], s_next[tid]);
     // per digit (one thread each): offsets over warps and the tile count
     uint32_t count = 0;
     for (int w = 0; w < kSortThreads / 32; ++w) {
@@ -533,19 +548,36 @@ tie_fixup_kernel(const uint32_t* __restrict__ key, const Vec4<R>* __restrict__ p
     for (int r = threadIdx.x; r < nruns; r += kFixThreads) {
         const int64_t s = base + s_runs[r];
         const uint32_t k = s_key[s_runs[r] + 1];
-        // last member: the keys are sorted, so search for the last position
-        // holding k (doubling steps, then bisection; key[s + 1] == k)
-        int64_t lo = s + 1, hi = N, step = 1;
-        for (;;) {
-            const int64_t probe = lo + step;
-            if (probe >= N || key[probe] != k) { hi = probe < N ? probe : N; break; }
-            lo = probe;
-            step <<= 1;
-        }
-        while (hi - lo > 1) {
-            const int64_t mid = lo + (hi - lo) / 2;
-            if (key[mid] == k) lo = mid;
-            else hi = mid;
+        // last member: the keys are sorted, so it is the last position
+        // holding k.  A run that ends inside the tile is found by bisection
+        // over the staged keys (s_key[j + 1] is the key of local index j);
+        // only a run that reaches the tile's end continues with doubling
+        // steps and bisection over the keys in global memory.
+        int64_t lo;
+        if (s_key[nt] != k) {
+            int a = s_runs[r] + 1, b = nt - 1;   // key(a) == k, key(b) != k
+            while (b - a > 1) {
+                const int mid = a + (b - a) / 2;
+                if (s_key[mid + 1] == k) a = mid;
+                else b = mid;
+            }
+            lo = base + a;
+        } else if (s_key[nt + 1] != k) {
+            lo = base + nt - 1;
+        } else {
+            lo = base + nt;                       // key[lo] == k
+            int64_t hi = N, step = 1;
+            for (;;) {
+                const int64_t probe = lo + step;
+                if (probe >= N || key[probe] != k) { hi = probe < N ? probe : N; break; }
+                lo = probe;
+                step <<= 1;
+            }
+            while (hi - lo > 1) {
+                const int64_t mid = lo + (hi - lo) / 2;
+                if (key[mid] == k) lo = mid;
+                else hi = mid;
+            }
         }
         const int64_t len = lo - s + 1;
         if (len <= kFixLocal) {
@@ -614,10 +646,12 @@ int radial_sort_impl(const void* posm, int64_t N, const SortBuffers& b, const La
     uint32_t *kin = b.keys_a, *vin = b.vals_a, *kout = b.keys_b, *vout = b.vals_b;
     for (int pass = 0; pass < 4; ++pass) {
         const uint32_t* vals_in = pass == 0 ? nullptr : vin;
+        // passes 0 and 1 count the histograms of digits 1 and 2
+        uint32_t* next_hist = pass < 2 ? b.hist + (pass + 1) * 256 : nullptr;
         if (launch_pdl(onesweep_kernel, dim3(nst), dim3(kSortThreads), 0, ctx.stream, (const uint32_t*)kin,
                        vals_in, kout, vout, (const uint32_t*)(b.hist + pass * 256),
                        b.status + (size_t)pass * (nst + kStatusPad) * 256, b.counters + pass, 8 * pass,
-                       N, ctx.wait_limit > 0 ? ctx.wait_limit : kSpinLimit, ctx.err))
+                       N, ctx.wait_limit > 0 ? ctx.wait_limit : kSpinLimit, next_hist, ctx.err))
             return ETICS_ERR_CUDA;
         ++*ctx.launches;
         uint32_t* t = kin; kin = kout; kout = t;
@@ -658,7 +692,7 @@ int lookback_timeout_probe(void* ws, int64_t spins, const LaunchCtx& ctx) {
     ++*ctx.launches;
     onesweep_kernel<<<1, kSortThreads, 0, ctx.stream>>>(b.keys_a, nullptr, b.keys_b, b.vals_b,
                                                          b.hist, b.status, b.counters, 0,
-                                                         kTimeoutProbeN, spins, ctx.err);
+                                                         kTimeoutProbeN, spins, nullptr, ctx.err);
     if (cudaGetLastError()) return ETICS_ERR_CUDA;
     ++*ctx.launches;
     return ETICS_OK;
