@@ -1026,6 +1026,49 @@ def run_sweep(args):
             "fp32_peak_note": FP32_PEAK_NOTE, "N": sweep_n, "l_max": sweep_l, "n_max": sweep_nmax}
 
 
+def run_coeffprec(args):
+    """Precision of the mixed coefficient passes against the FP64 paths
+    (Sec. 2.4 eq. 18 coefficients; the mixed path accumulates FP32 products in
+    FP64 blocks): max |c_mixed - c_fp64| / max |c_fp64| and the largest
+    deviations with their (n, l, m), for the bar-perturbed Hernquist model at
+    N = 2^20 .. 2^26 and (n_max, l_max) = (10, 6) and (14, 8), both at the
+    same FP32-rounded positions; at N <= 2^22 also both against the FP64
+    oracle."""
+    import torch
+    import oracle
+    from paper_1406_4254_gb300 import etics, inputs
+    out = {"experiment": "coeffprec", "model": "hernquist + 5% l=2,m=2 bar (seed 3)", "rows": []}
+    for k in (20, 22, 24, 26):
+        n = 1 << k
+        pm, _ = inputs.hernquist_bar(n, seed=3, eps=0.05, velocities=False)
+        pm32 = pm.astype(np.float32)
+        del pm
+        x = torch.tensor(pm32, device="cuda")
+        for nm, lm in ((10, 6), (14, 8)):
+            c32 = etics.scf_coeffs(x, nm, lm).cpu().numpy()
+            c64 = etics.scf_coeffs(x.double(), nm, lm).cpu().numpy()
+            scale = float(np.max(np.abs(c64)))
+            dev = np.abs(c32 - c64)
+            top = []
+            for f in np.argsort(dev.ravel())[::-1][:3]:
+                nn, j = divmod(int(f), c64.shape[1])
+                l = int(np.sqrt(j))
+                top.append({"n": nn, "l": l, "m": j - l * l - l, "dev": float(dev[nn, j]),
+                            "c_fp64": float(c64[nn, j])})
+            row = {"N": n, "n_max": nm, "l_max": lm, "max_dev_over_max_c": float(dev.max()) / scale,
+                   "largest": top}
+            if k <= 22:
+                p64 = pm32.astype(np.float64)
+                cor = oracle.scf_coeffs(p64[:, :3], p64[:, 3], nm, lm)
+                row["fp64_vs_oracle"] = float(np.max(np.abs(c64 - cor))) / scale
+                row["mixed_vs_oracle"] = float(np.max(np.abs(c32 - cor))) / scale
+            out["rows"].append(row)
+        etics.check_error()
+        del x
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_peaks(args):
     """FP32 and FP64 FMA rates of the GPU (the roofline denominators of the
     arithmetic-bound kernels), from etics_fma_peak: as a burst (best of 5
@@ -1086,7 +1129,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=65536)
     ap.add_argument("--experiment", choices=["leapfrog", "batch", "surrogate", "accuracy", "gemm",
-                                             "sweep", "peaks"],
+                                             "sweep", "peaks", "coeffprec"],
                     default=None)
     ap.add_argument("--gemm-mnk", type=int, nargs=3, default=[16384, 4096, 4096])
     ap.add_argument("--acc-n", type=int, nargs="+", default=[1000, 10000, 100000, 1000000])
@@ -1116,6 +1159,9 @@ def main():
         return
     if args.experiment == "peaks":
         emit(run_peaks(args))
+        return
+    if args.experiment == "coeffprec":
+        emit(run_coeffprec(args))
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
