@@ -667,7 +667,54 @@ def run_batch(args):
         t1.record()
         torch.cuda.synchronize()
         tg.append(t0.elapsed_time(t1))
+    # the plain FP64-GPU form: the same systems through the FP64 per-system
+    # calls (eager and graph-captured) and through an FP64 batch
+    x64 = x.double()
+    views64 = [x64[plan.particle_offsets[i]:plan.particle_offsets[i + 1]]
+               for i in range(len(sizes))]
+    cs64 = [torch.empty_like(c) for c in cs]
+    outs64 = [torch.empty_like(v) for v in views64]
+    ws64 = etics.workspace(max(sizes), 14, 8, etics.SCF, etics.FP64)
+
+    def loop64():
+        for i in range(len(sizes)):
+            etics.scf_coeffs(views64[i], nm[i], lm[i], out=cs64[i], ws=ws64)
+            etics.scf_field(views64[i], cs64[i], nm[i], lm[i], out=outs64[i])
+
+    def timed(fn, reps):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            t0.record()
+            fn()
+            t1.record()
+            torch.cuda.synchronize()
+            ts.append(t0.elapsed_time(t1))
+        return statistics.mean(ts)
+
+    t64_eager = timed(loop64, max(3, args.steps // 2))
+    g3 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g3):
+        loop64()
+    t64_graph = timed(g3.replay, max(3, args.steps // 2))
+    plan64 = etics.BatchPlan(sizes, nm, lm, precision=etics.FP64)
+    coeffs64b = torch.empty(plan64.coeff_count, dtype=torch.float64, device="cuda")
+    out64b = torch.empty_like(x64)
+    with torch.cuda.stream(side):
+        etics.scf_batch(x64, plan64, coeffs=coeffs64b, out=out64b)
+    torch.cuda.current_stream().wait_stream(side)
+    g4 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g4):
+        etics.scf_batch(x64, plan64, coeffs=coeffs64b, out=out64b)
+    t64_batch = timed(g4.replay, max(3, args.steps // 2))
     etics.check_error()
+    # eq. 23 force error of the batched mixed-precision forces against the
+    # FP64 per-system forces, every particle of every system
+    a_mixed = out[:, :3].double().cpu().numpy()
+    a_fp64 = torch.cat(outs64)[:, :3].cpu().numpy()
+    acc_vs_fp64 = eps_stats(a_mixed, a_fp64)
     # agreement of the two paths
     err = 0.0
     for i in range(0, len(sizes), 17):
@@ -683,6 +730,13 @@ def run_batch(args):
                                     "kernel_launches": 3 * len(sizes)},
             "one_call_per_system_graph": {"ms": statistics.mean(tg),
                                           "particle_forces_per_s": ntot / (statistics.mean(tg) * 1e-3)},
+            "fp64_one_call_per_system": {"ms": t64_eager,
+                                         "particle_forces_per_s": ntot / (t64_eager * 1e-3)},
+            "fp64_one_call_per_system_graph": {"ms": t64_graph,
+                                               "particle_forces_per_s": ntot / (t64_graph * 1e-3)},
+            "fp64_batched_graph": {"ms": t64_batch, "particle_forces_per_s": ntot / (t64_batch * 1e-3)},
+            "speedup_vs_fp64_calls": t64_eager / mb, "speedup_vs_fp64_graph_of_calls": t64_graph / mb,
+            "batched_mixed_force_error_vs_fp64_calls": acc_vs_fp64,
             "speedup": ml / mb, "speedup_vs_graph_of_calls": statistics.mean(tg) / mb,
             "tuning": tuning.as_dict(), "tuned_in_this_run": tuned_now,
             "max_rel_coeff_diff_batched_vs_single": err}

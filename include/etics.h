@@ -143,11 +143,12 @@ int etics_radial_keys(const void *posm, int64_t N, int precision, uint32_t *keys
  * items[i].n consecutive particles; its coefficients are packed one system
  * after another (n_max+1)(l_max+1)^2 each, in the layout of etics_scf_coeffs. */
 typedef struct { int64_t n; int n_max; int l_max; } etics_batch_item;
-/* Launch shape (0 = default): particles per coefficient tile (multiple of 4,
- * 8..128; FP64 plans with tile > 64 exceed one block's shared memory and are
- * rejected with ETICS_ERR_UNSUPPORTED), coefficient blocks per SM (1..8),
- * field threads per block (multiple of 32, <= 256), particles per field work
- * item (>= 1). */
+/* Launch shape (0 = default): particles per coefficient tile -- mixed
+ * precision: 8..512, rounded up to a multiple of 64 (default 512); FP64:
+ * multiple of 4, 8..128 (default 32; tiles > 64 exceed one block's shared
+ * memory and are rejected with ETICS_ERR_UNSUPPORTED) -- coefficient blocks
+ * per SM (1..8), field threads per block (multiple of 32, <= 256), particles
+ * per field work item (>= 1). */
 typedef struct { int tile; int blocks_per_sm; int field_threads; int field_chunk; } etics_batch_tuning;
 
 /* Builds the batch plan in HOST memory.  With plan == NULL only the sizes are

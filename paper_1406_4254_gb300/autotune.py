@@ -22,8 +22,10 @@ from . import etics
 
 TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "autotune.json")
 
+# tiles: 64 serves both precisions; mixed-precision plans also take 256 and
+# 512 (FP64 plans reject tiles above 128, and the tuner skips those)
 CANDIDATES = {
-    "tile": [32, 64, 128],
+    "tile": [64, 256, 512],
     "blocks_per_sm": [1, 2, 3],
     "field_threads": [128, 256],
     "field_chunk": [1024, 4096],

@@ -135,3 +135,84 @@ def test_pair_plans_split_each_level_evenly_and_invert(tmp_path):
             assert max(w) - min(w) <= 1 and sum(w) == 2 * l + 1, (lm, cap, l, w)
         nc_order = [nc for _, _, nc in p["bins"]]
         assert nc_order == sorted(nc_order, reverse=True)
+
+
+LAYOUT_PROGRAM = r"""
+#include "etics_batch_layout.h"
+#include <cstdio>
+int main() {
+    static etics::BatchLayout lay;
+    printf("K %d %d %d\n", etics::kBpThreads, etics::kBpCap, etics::kBpMaxBins);
+    for (int lm = 0; lm <= etics::kBatchLM; ++lm) {
+        etics::batch_layout(lm, lay);
+        printf("LM %d %d\n", lm, lay.nbins);
+        for (int b = 0; b < lay.nbins; ++b)
+            printf("B %d %d %d %d %d\n", lay.bin[b].level, lay.bin[b].col0, lay.bin[b].nc,
+                   lay.bin[b].lane0, lay.bin[b].nlanes);
+        for (int j = 0; j < etics::kBpThreads; ++j)
+            printf("L %d %d %d %d %d %d\n", lay.lane[j].col[0], lay.lane[j].col[1],
+                   lay.lane[j].col[2], lay.lane[j].level, lay.lane[j].rank, lay.lane[j].nlanes);
+    }
+    return 0;
+}
+"""
+
+
+def test_batch_lane_layouts(tmp_path):
+    """The mixed-precision batch pass: for every l_max the bins cover each
+    dense column l*l + c exactly once, one level per bin, at most three
+    columns, each level split evenly; every lane belongs to one bin (ranks
+    0..nlanes-1 on consecutive lanes), the shares differ by at most one lane,
+    and the bin's lanes take each particle pair of a tile exactly once."""
+    gxx = shutil.which("g++")
+    if not gxx:
+        pytest.skip("g++ not available")
+    src, exe = tmp_path / "layout.cpp", tmp_path / "layout"
+    src.write_text(LAYOUT_PROGRAM)
+    r = subprocess.run([gxx, "-std=c++17", "-I", CSRC, "-o", str(exe), str(src)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-2000:]
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    lays, cur, consts = {}, None, None
+    for line in out.splitlines():
+        f = list(map(int, line.split()[1:]))
+        if line.startswith("K"):
+            consts = f
+        elif line.startswith("LM"):
+            cur = {"nbins": f[1], "bins": [], "lanes": []}
+            lays[f[0]] = cur
+        elif line.startswith("B"):
+            cur["bins"].append(tuple(f))
+        else:
+            cur["lanes"].append(tuple(f))
+    threads, cap, maxbins = consts
+    assert sorted(lays) == list(range(9))
+    for lm, lay in lays.items():
+        bins = lay["bins"]
+        assert len(bins) == lay["nbins"] == sum(-(-(2 * l + 1) // cap) for l in range(lm + 1))
+        assert len(bins) <= maxbins
+        seen, widths = set(), {}
+        for l, col0, nc, lane0, nl in bins:
+            assert 1 <= nc <= cap and l * l <= col0 and col0 + nc <= (l + 1) * (l + 1)
+            widths.setdefault(l, []).append(nc)
+            for j in range(col0, col0 + nc):
+                assert j not in seen
+                seen.add(j)
+        assert seen == set(range((lm + 1) ** 2))
+        for l, w in widths.items():
+            assert max(w) - min(w) <= 1 and sum(w) == 2 * l + 1
+        shares = [nl for *_, nl in bins]
+        assert sum(shares) == threads and max(shares) - min(shares) <= 1
+        lanes = lay["lanes"]
+        assert len(lanes) == threads
+        nxt = 0
+        for l, col0, nc, lane0, nl in bins:
+            assert lane0 == nxt
+            nxt += nl
+            for r in range(nl):
+                c0, c1, c2, lev, rank, nls = lanes[lane0 + r]
+                assert (lev, rank, nls) == (l, r, nl)
+                assert [c0, c1, c2] == [col0 + (c if c < nc else 0) for c in range(cap)]
+            for tp in (32, 96, 256):
+                pairs = sorted(p for r in range(nl) for p in range(r, tp, nl))
+                assert pairs == list(range(tp))
