@@ -746,15 +746,20 @@ def run_surrogate(args):
     """Surrogate-accelerated SCF: a Hernquist sphere with a 5% l = 2, m = 2
     bar perturbation (N = 2^26 by default), SCF (14, 8), KDK at dt = 0.005.
     A plain-SCF run of --sur-steps steps produces the coefficient trajectory;
-    the per-coefficient MLP (8 -> 256 -> 256 -> 1, bf16 weights, FP32
-    accumulation) is trained on its first 75% by the library's kernels and
-    validated one step ahead on the rest.  From the final state three
-    continuations of --sur-eval steps are timed: plain SCF every step, the
-    forecast on 3 of every 4 steps (plain SCF on the 4th, judging the forecast
-    against the force-error budget: median <= 1e-5, 99th percentile <= 1e-4,
-    on 4096 particles), and plain reuse of the last coefficients on 3 of 4
-    steps (judged the same way).  An
-    untimed pass then measures each substep's relative force error (eq. 23)
+    on its first 75% the library's kernels fit, for each coefficient and each
+    horizon k = 1..S (S = --sur-stride), a linear predictor of the vector k
+    steps after a history of eight true vectors spaced S apart (least
+    squares, FP64), and train the per-coefficient MLP (8 -> 256 -> 256 -> S,
+    bf16 weights, FP32 accumulation) on what those miss; both are validated
+    on the rest.  From the final state four continuations of --sur-eval steps
+    are timed: plain SCF every step; the coefficient pass on every S-th step
+    only and the forecast on the others (judging, on each recompute step, the
+    forecast it would have used against the force-error budget: median <=
+    1e-5, 99th percentile <= 1e-4, on 4096 particles; a miss makes the next
+    block plain SCF); the same with the fitted predictors alone (no network);
+    and plain reuse of the last coefficients on the other steps (judged the
+    same way).  An
+    untimed pass then measures each forecast step's relative force error (eq. 23)
     against plain SCF at the same positions on a 65536-particle sample."""
     import torch
     from paper_1406_4254_gb300 import etics, inputs, surrogate
@@ -775,14 +780,15 @@ def run_surrogate(args):
     ms_traj = ev0.elapsed_time(ev1) / args.sur_steps
     T = traj.shape[0]
     n_train = int(0.75 * T)
-    fc = surrogate.Forecaster(n_max, l_max, hidden=256, seed=args.seed)
+    S = args.sur_stride
+    fc = surrogate.Forecaster(n_max, l_max, stride=S, hidden=256, seed=args.seed)
     ev0.record()
     losses = fc.fit(traj[:n_train], iters=args.sur_iters, batch=16, lr=1e-3, seed=args.seed,
                     log_every=max(1, args.sur_iters // 10))
     ev1.record()
     torch.cuda.synchronize()
     ms_train = ev0.elapsed_time(ev1)
-    hold, lin, cubic, net = fc.one_step_errors(traj, n_train)
+    he = fc.horizon_errors(traj, n_train)
     med = lambda a: float(np.median(a))  # noqa: E731
     m = x[:, 3].double()
 
@@ -791,7 +797,7 @@ def run_surrogate(args):
                      + 0.5 * (m * aa[:, 3].double()).sum())
 
     modes = {}
-    for mode in ("plain", "forecast", "hold"):
+    for mode in ("plain", "forecast", "fitted", "hold"):
         xs, vs, accs = x.clone(), v.clone(), acc.clone()
         fc.reset(traj)
         e0 = energy(vs, accs)
@@ -802,7 +808,7 @@ def run_surrogate(args):
                 etics.leapfrog_step(xs, vs, accs, dt, etics.SCF, n_max, l_max)
             st = None
         else:
-            st = surrogate.run(xs, vs, accs, args.sur_eval, dt, fc, period=4, mode=mode)
+            st = surrogate.run(xs, vs, accs, args.sur_eval, dt, fc, mode=mode)
         ev1.record()
         torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1) / args.sur_eval
@@ -812,23 +818,23 @@ def run_surrogate(args):
             modes[mode].update({"recomputes": st.recomputes, "forecast_steps": st.forecasts,
                                 "fallback_blocks": st.fallbacks,
                                 "checks": len(st.checks),
-                                "check_frac_above_median_budget": med([c[1] for c in st.checks[1:]])
-                                if len(st.checks) > 1 else None,
-                                "check_frac_above_p99_budget": med([c[2] for c in st.checks[1:]])
-                                if len(st.checks) > 1 else None})
+                                "check_frac_above_median_budget": med([c[1] for c in st.checks])
+                                if st.checks else None,
+                                "check_frac_above_p99_budget": med([c[2] for c in st.checks])
+                                if st.checks else None})
         del xs, vs, accs
-    for mode in ("forecast", "hold"):
+    for mode in ("forecast", "fitted", "hold"):
         modes[mode]["speedup_vs_plain"] = modes["plain"]["ms_per_step"] / modes[mode]["ms_per_step"]
     # untimed accuracy pass: every substep against plain SCF at the same positions
     s_n = min(65536, n)
-    for mode in ("forecast", "hold"):
+    for mode in ("forecast", "fitted", "hold"):
         xs, vs, accs = x.clone(), v.clone(), acc.clone()
         fc.reset(traj)
-        per_sub = {1: [], 2: [], 3: []}
+        per_sub = {k: [] for k in range(1, S)}
         a_ref = torch.empty((s_n, 4), dtype=torch.float32, device=dev)
         a_use = torch.empty_like(a_ref)
 
-        def hook(t, kind, c_use):
+        def hook(t, kind, c_use, hz):
             if kind == "recompute":
                 return
             c_true = etics.scf_coeffs(xs, n_max, l_max)
@@ -837,11 +843,10 @@ def run_surrogate(args):
             a = a_use.double().cpu().numpy()[:, :3]
             r = a_ref.double().cpu().numpy()[:, :3]
             e = np.linalg.norm(a - r, axis=1) / np.linalg.norm(r, axis=1)
-            per_sub[t % 4].append((float(np.median(e)), float(np.quantile(e, 0.99)),
-                                   float(e.max())))
+            per_sub[hz].append((float(np.median(e)), float(np.quantile(e, 0.99)),
+                                float(e.max())))
 
-        surrogate.run(xs, vs, accs, min(args.sur_eval, 200), dt, fc, period=4, mode=mode,
-                      hook=hook)
+        surrogate.run(xs, vs, accs, min(args.sur_eval, 200), dt, fc, mode=mode, hook=hook)
         modes[mode]["force_error_by_substep"] = {
             str(k): {"median": med([p[0] for p in v_]), "p99": med([p[1] for p in v_]),
                      "max": float(max(p[2] for p in v_)), "samples": len(v_)}
@@ -878,13 +883,14 @@ def run_surrogate(args):
             "workload": f"hernquist + 5% l=2 m=2 bar, N={n}, SCF(14,8), KDK dt={dt}",
             "trajectory": {"steps": args.sur_steps, "plain_ms_per_step": ms_traj,
                            "initial_conditions_s": t_ic},
-            "training": {"network": "per-coefficient 8->256->256->1, tanh, bf16 x bf16 -> FP32",
+            "training": {"network": f"per-coefficient 8->256->256->{S}, tanh, bf16 x bf16 -> FP32",
                          "train_vectors": n_train, "iters": args.sur_iters,
                          "histories_per_batch": 16, "ms": ms_train, "loss_log": losses},
-            "one_step_error_validation": {"hold": med(hold), "linear": med(lin),
-                                          "cubic": med(cubic), "mlp": med(net),
-                                          "unit": "|c_hat - c| / |c - c_prev|, median"},
-            "budget": {"median": 1e-5, "p99": 1e-4, "sample": 4096, "period": 4},
+            "horizon_error_validation": {
+                str(k): {"hold": med(d["hold"]), "cubic": med(d["cubic"]),
+                         "fitted_linear_predictor": med(d["fitted"]), "fitted_plus_mlp": med(d["net"])}
+                for k, d in he.items()} | {"unit": "|c_hat - c_{t+k}| / |c_{t+k} - c_t|, median"},
+            "budget": {"median": 1e-5, "p99": 1e-4, "sample": 4096, "stride": S},
             "rollout_steps": args.sur_eval, "modes": modes,
             "plain_fp64": {"ms_per_step": ms64, "steps": k64},
             "plain_mixed_split_ms": {"coefficients": ms_coef, "field": ms_field}}
@@ -1192,6 +1198,7 @@ def main():
     ap.add_argument("--sur-steps", type=int, default=2000)
     ap.add_argument("--sur-eval", type=int, default=400)
     ap.add_argument("--sur-iters", type=int, default=3000)
+    ap.add_argument("--sur-stride", type=int, default=3)
     args = ap.parse_args()
     if args.experiment == "surrogate":
         emit(run_surrogate(args))

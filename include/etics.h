@@ -249,11 +249,27 @@ int etics_mlp_adam(const etics_mlp_shape *shape, float *params, const float *gra
 int etics_mlp_to_bf16(const etics_mlp_shape *shape, const float *params, uint16_t *params_bf16,
                       void *stream);
 
-/* Normalisers of a coefficient trajectory traj (device, T x D doubles, T >= 5)
- * into norm (device, 7 x D doubles): mean, 1/standard deviation, 1/RMS of the
- * k-th backward differences for k = 1..4, and the RMS s4 of the fourth
- * differences (a reciprocal is 0 where its scale is 0). */
-int etics_coeff_stats(const double *traj, int T, int D, double *norm, void *stream);
+/* Coefficient forecasting glue.  A forecast works on a history of eight true
+ * coefficient vectors c_0..c_7 (oldest first) spaced `stride` steps apart
+ * (1 <= stride <= 4) and predicts the vector k steps after c_7 for each
+ * horizon k = 1..stride: the cubic through c_4..c_7 evaluated at
+ * s = k/stride of a spacing after c_7, ((c_7 + s d1) + s(s+1)/2 d2) +
+ * s(s+1)(s+2)/6 d3 (backward differences of the history at c_7), plus a
+ * per-coefficient linear correction fitted to the trajectory, plus the
+ * network's correction.
+ *
+ * Normalisers and fitted predictors of a trajectory traj (device, T x D
+ * doubles, T >= 5) into norm (device, (7 + 9 stride) x D doubles): rows 0-6
+ * the mean, 1/standard deviation, 1/RMS of the k-th backward differences at
+ * spacing `stride` (k = 1..4) and their RMS s4 (a reciprocal is 0 where its
+ * scale is 0); then per horizon k, from row 7 + 9(k-1): beta_k[0..6], the RMS
+ * q_k of its residual and 1/q_k.  The predictor of horizon k regresses
+ * t_k = (c_{t+k} - cubic_k) / s4 by least squares on the regressors u of the
+ * history (the seven feature blocks 1-7 of etics_coeff_features before their
+ * bf16 rounding) over every history of traj whose horizons lie inside it,
+ * with a 1e-12 relative ridge; beta = 0 and q = 1 where there is none.  Two
+ * kernels. */
+int etics_coeff_stats(const double *traj, int T, int D, int stride, double *norm, void *stream);
 /* Network inputs x (bf16 codes) of the histories store[rows[b][0..7]]
  * (device int32, oldest first; store: device, rows of D doubles), eight
  * blocks per coefficient from the backward differences d1..d4 of the history:
@@ -262,24 +278,26 @@ int etics_coeff_stats(const double *traj, int T, int D, double *norm, void *stre
  * ETICS_FEAT_JOINT: x is batch x 8D, element [b][blk*D + j] (one network row
  * sees every coefficient); ETICS_FEAT_PER_COEFF: x is (batch*D) x 8, element
  * [b*D + j][blk] (one row per coefficient, a network shared by all
- * coefficients).  With next_rows (nullable, device int32[batch]) also the
- * training targets (batch x D FP32 in both layouts): the next fourth
- * difference over its RMS, i.e. what cubic extrapolation misses. */
+ * coefficients).  With next_rows (nullable, device int32[batch][stride]: the
+ * vectors 1..stride steps after each history) also the training targets
+ * (FP32): for horizon k, (t_k - beta_k . u) / q_k, what the fitted predictor
+ * misses, at [(b*D + j)*stride + k-1] (per coefficient) or
+ * [(b*stride + k-1)*D + j] (joint). */
 #define ETICS_FEAT_JOINT 0
 #define ETICS_FEAT_PER_COEFF 1
 int etics_coeff_features(const double *store, const int32_t *rows, const int32_t *next_rows,
-                         int batch, int D, const double *norm, int layout, uint16_t *x,
-                         float *target, void *stream);
-/* The next coefficient vector of a ring of 8 (ring: device 8 x D doubles;
- * order: device int32[8], slots oldest..newest): coeffs_in when non-NULL, else
- * the cubic extrapolation c7 + d1 + d2 + d3 of the ring plus s4 * y, from the
- * network output y (device FP32[D]; exactly one of coeffs_in, y).  With
- * commit != 0 the vector is written into the oldest slot and order rotated in
- * place; coeffs_out (nullable when commit != 0) receives it.  One block;
- * graph-capturable. */
-int etics_coeff_advance(double *ring, int32_t *order, int D, const double *coeffs_in,
-                        const float *y, const double *norm, double *coeffs_out, int commit,
-                        void *stream);
+                         int batch, int D, int stride, const double *norm, int layout,
+                         uint16_t *x, float *target, void *stream);
+/* A forecast or a push on a ring of 8 vectors (ring: device 8 x D doubles;
+ * order: device int32[8], slots oldest..newest).  Forecast (y non-NULL,
+ * 1 <= horizon <= stride): cubic_k + s4 (beta_k . u + q_k y[j*y_stride]) for
+ * the network output y (device FP32).  Push (coeffs_in non-NULL): coeffs_in.
+ * Exactly one of coeffs_in, y.  With commit != 0 the vector is written into
+ * the oldest slot and order rotated in place; coeffs_out (nullable when
+ * commit != 0) receives it.  One block; graph-capturable. */
+int etics_coeff_advance(double *ring, int32_t *order, int D, int stride, int horizon,
+                        const double *coeffs_in, const float *y, int y_stride,
+                        const double *norm, double *coeffs_out, int commit, void *stream);
 
 /* Relative acceleration error e_i = |a_i - r_i| / |r_i| (Sec. 4.2) of
  * accpot a against accpot r (device (N,4) arrays of the given precision):

@@ -20,10 +20,11 @@ error entering a product are rounded to bf16; sums stay in FP64 here.  With
 ``quantize=False`` the whole network is FP64.
 
 Forecast features (``features``) and the forecast update (``advance``) are
-defined on a history of coefficient vectors c_0 .. c_7 (oldest first) through
-its backward differences, each a single FP64 subtraction of the previous
-order: d1_k = c_k - c_{k-1}, d2_k = d1_k - d1_{k-1}, d3_k = d2_k - d2_{k-1},
-d4_k = d3_k - d3_{k-1}.  Eight blocks per coefficient:
+defined on a history of eight true coefficient vectors c_0 .. c_7 (oldest
+first) spaced ``stride`` steps apart, through its backward differences, each a
+single FP64 subtraction of the previous order: d1_i = c_i - c_{i-1},
+d2_i = d1_i - d1_{i-1}, d3_i = d2_i - d2_{i-1}, d4_i = d3_i - d3_{i-1}.
+Eight blocks per coefficient:
 
 * block 0: (c_7 - mu) * inv_sigma                  (the state),
 * blocks 1, 2, 3: d1_7 * inv_s1, d2_7 * inv_s2, d3_7 * inv_s3,
@@ -32,12 +33,22 @@ d4_k = d3_k - d3_{k-1}.  Eight blocks per coefficient:
 each rounded to float32 and then to bf16 (both round-to-nearest-even), laid
 out block-major in one row per history (the joint network sees every
 coefficient) or as one row of 8 per coefficient (a network shared by all
-coefficients).  The base forecast of c_8 is the cubic extrapolation
-P = ((c_7 + d1_7) + d2_7) + d3_7; the network learns what it misses, the
-next fourth difference: the training target for a next vector c_8 is
-d4_8 * inv_s4 rounded to float32 (d1_8 = c_8 - c_7 and so on), and
-``advance`` forms c_8 = P + s4 * y.  All FP64 operations are single roundings
-in the order written.
+coefficients); s_k are the RMS of the k-th differences at that spacing.  The
+forecast of the vector k steps after c_7 (horizon k = 1..stride) starts from
+the cubic through c_4..c_7 at s = k / stride of a spacing (Newton's backward
+form): P_k = ((c_7 + s d1_7) + a2 d2_7) + a3 d3_7 with a2 = (s (s+1)) / 2,
+a3 = (a2 (s+2)) / 3.  A linear predictor fitted to the trajectory for each
+coefficient and horizon corrects it: its regressors u_0..u_6 are the blocks
+1..7 in FP64 (before rounding), its target t_k = (c_{t+k} - P_k) * inv_s4,
+and ``stats`` fits beta_k by least squares over every history of the
+trajectory whose horizons lie inside it (normal equations with a ridge of
+1e-12 times the mean diagonal; beta = 0 where the Gram matrix vanishes) and
+records the RMS q_k of the residual t_k - beta_k . u (summed left to right).
+The network learns what the fitted predictor misses: the training target of
+horizon k is (t_k - beta_k . u) * inv_q_k rounded to float32, and
+``advance`` forms P_k + s4 * (beta_k . u + q_k * y).  Without a history
+beta = 0 and q = 1.  All FP64 operations are single roundings in the order
+written.
 
 Pins: ``tests/test_oracle_mlp.py`` (finite differences, closed forms of a
 linear layer and of Adam under a constant gradient, brute-force loops, exact
@@ -153,36 +164,106 @@ def adam(params, grads, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
 # forecast glue
 # ---------------------------------------------------------------------------
 HIST = 8
-NORM_ROWS = 7     # mu, inv_sigma, inv_s1, inv_s2, inv_s3, inv_s4, s4
+LIN_FEAT = 7
+RIDGE = 1e-12
 
 
-def _diff(c):
-    return c[1:] - c[:-1]
+def norm_rows(stride):
+    """Rows of the normaliser array: 7 scales, then 9 per horizon."""
+    return 7 + 9 * stride
 
 
-def stats(traj):
+def _beta_row(k):
+    return 7 + 9 * (k - 1)
+
+
+def _inv(s):
+    out = np.zeros_like(s)
+    nz = s > 0
+    out[nz] = 1.0 / s[nz]
+    return out
+
+
+def stats(traj, stride=1):
     """Normalisers of a coefficient trajectory (T x D, T >= 5): mean mu,
     population standard deviation sigma and the RMS s_k of the k-th backward
-    differences (k = 1..4) of every coefficient; inv_* = 1/s, or 0 where
-    s == 0.  Returns the NORM_ROWS x D array
-    (mu, inv_sigma, inv_s1, inv_s2, inv_s3, inv_s4, s4)."""
+    differences at spacing ``stride`` (k = 1..4, over every index where they
+    exist) of every coefficient; inv_* = 1/s, or 0 where s == 0; then per
+    horizon the fitted linear predictor (see the module notes).  Returns the
+    norm_rows(stride) x D array (mu, inv_sigma, inv_s1..inv_s4, s4, then per
+    horizon k: beta_k[0..6], q_k, inv_q_k)."""
     c = np.asarray(traj, dtype=np.float64)
+    T, D = c.shape
     mu = c.mean(axis=0)
     sigma = np.sqrt(((c - mu) ** 2).mean(axis=0))
-
-    def inv(s):
-        out = np.zeros_like(s)
-        nz = s > 0
-        out[nz] = 1.0 / s[nz]
-        return out
-    rows = [mu, inv(sigma)]
+    rows = [mu, _inv(sigma)]
     d = c
     for _ in range(4):
-        d = _diff(d)
-        s = np.sqrt((d * d).mean(axis=0))
-        rows.append(inv(s))
+        d = d[stride:] - d[:-stride]
+        s = np.sqrt((d * d).mean(axis=0)) if len(d) else np.zeros(D)
+        rows.append(_inv(s))
     rows.append(s)
-    return np.stack(rows)
+    norm = np.concatenate([np.stack(rows), np.zeros((norm_rows(stride) - 7, D))])
+    _fit_linear(c, stride, norm)
+    return norm
+
+
+def _regressors(dd, norm):
+    """The regressors u_0..u_6 of a history (differences at c_7)."""
+    is1, is2, is3, is4 = norm[2], norm[3], norm[4], norm[5]
+    return [dd[1][7] * is1, dd[2][7] * is2, dd[3][7] * is3,
+            dd[4][7] * is4, dd[4][6] * is4, dd[4][5] * is4, dd[4][4] * is4]
+
+
+def _lin_predict(u, norm, k):
+    b = _beta_row(k)
+    s = norm[b] * u[0]
+    for i in range(1, LIN_FEAT):
+        s = s + norm[b + i] * u[i]
+    return s
+
+
+def cubic_base(c7, d1, d2, d3, k, stride):
+    """The cubic through the history's last four vectors, k/stride of a
+    spacing after c_7."""
+    s = float(k) / float(stride)
+    a2 = (s * (s + 1.0)) * 0.5
+    a3 = (a2 * (s + 2.0)) / 3.0
+    return ((c7 + s * d1) + a2 * d2) + a3 * d3
+
+
+def _fit_linear(c, stride, norm):
+    """Per horizon k = 1..stride: beta_k from the normal equations over every
+    history with its horizons inside the trajectory, then q_k and 1/q_k."""
+    T, D = c.shape
+    ts = list(range((HIST - 1) * stride, T - stride))
+    for k in range(1, stride + 1):
+        b = _beta_row(k)
+        if not ts:
+            norm[b:b + 7] = 0.0
+            norm[b + 7] = 1.0
+            norm[b + 8] = 1.0
+            continue
+        U = np.zeros((len(ts), LIN_FEAT, D))
+        tg = np.zeros((len(ts), D))
+        for w, t in enumerate(ts):
+            hist = [c[t - (HIST - 1 - i) * stride] for i in range(HIST)]
+            dd = _differences(hist)
+            U[w] = np.stack(_regressors(dd, norm))
+            base = cubic_base(hist[7], dd[1][7], dd[2][7], dd[3][7], k, stride)
+            tg[w] = (c[t + k] - base) * norm[5]
+        for j in range(D):
+            G = U[:, :, j].T @ U[:, :, j]
+            h = U[:, :, j].T @ tg[:, j]
+            tr = np.trace(G)
+            beta = np.zeros(LIN_FEAT)
+            if tr > 0:
+                beta = np.linalg.solve(G + RIDGE * tr / LIN_FEAT * np.eye(LIN_FEAT), h)
+            norm[b:b + 7, j] = beta
+        r = np.stack([tg[w] - _lin_predict(U[w], norm, k) for w in range(len(ts))])
+        q = np.sqrt((r * r).sum(axis=0) / len(ts))
+        norm[b + 7] = q
+        norm[b + 8] = _inv(q)
 
 
 def _differences(c):
@@ -195,17 +276,18 @@ def _differences(c):
     return d
 
 
-def features(store, rows, norm, next_rows=None, per_coeff=False):
+def features(store, rows, norm, next_rows=None, per_coeff=False, stride=1):
     """bf16 feature codes of the histories store[rows[b]] (rows: B x 8
     indices, oldest first): B x 8D (block-major per row) or, per coefficient,
-    (B*D) x 8 (one row per coefficient); with next_rows, float32 targets
-    (B x D)."""
+    (B*D) x 8 (one row per coefficient); with next_rows (B x stride: the
+    vectors 1..stride steps after each history), float32 targets, (B*D) x
+    stride per coefficient or B x (stride*D) (horizon-major) jointly."""
     store = np.asarray(store, dtype=np.float64)
     rows = np.asarray(rows)
-    mu, isg, is1, is2, is3, is4, _ = norm
+    mu, isg, is1, is2, is3, is4 = norm[:6]
     bsz, d = rows.shape[0], store.shape[1]
     x = np.zeros((bsz, HIST * d), dtype=np.uint16)
-    tgt = np.zeros((bsz, d), dtype=np.float32) if next_rows is not None else None
+    tgt = np.zeros((bsz, stride, d), dtype=np.float32) if next_rows is not None else None
     for b in range(bsz):
         c = [store[rows[b, k]] for k in range(HIST)]
         dd = _differences(c)
@@ -214,17 +296,26 @@ def features(store, rows, norm, next_rows=None, per_coeff=False):
             blocks.append(dd[4][k] * is4)
         x[b] = bf16_bits(np.concatenate(blocks))
         if next_rows is not None:
-            e = _differences(c + [store[next_rows[b]]])
-            tgt[b] = (e[4][8] * is4).astype(np.float32)
+            u = _regressors(dd, norm)
+            nr = np.asarray(next_rows).reshape(bsz, stride)
+            for k in range(1, stride + 1):
+                base = cubic_base(c[7], dd[1][7], dd[2][7], dd[3][7], k, stride)
+                tk = (store[nr[b, k - 1]] - base) * is4
+                tgt[b, k - 1] = ((tk - _lin_predict(u, norm, k)) * norm[_beta_row(k) + 8]).astype(np.float32)
     if per_coeff:
         x = x.reshape(bsz, HIST, d).transpose(0, 2, 1).reshape(bsz * d, HIST).copy()
+        if tgt is not None:
+            tgt = tgt.transpose(0, 2, 1).reshape(bsz * d, stride).copy()
+    elif tgt is not None:
+        tgt = tgt.reshape(bsz, stride * d)
     return x, tgt
 
 
-def advance(ring, order, norm, y=None, coeffs=None):
-    """Forecast (y given) or push (coeffs given) the next coefficient vector
-    into the ring of HIST vectors.  order: slots oldest..newest.  Returns
-    (new ring, new order, the vector written)."""
+def advance(ring, order, norm, y=None, coeffs=None, stride=1, horizon=1, commit=True):
+    """Forecast at ``horizon`` (y given, one value per coefficient) or push
+    (coeffs given) the next coefficient vector of the ring of HIST vectors.
+    order: slots oldest..newest.  Returns (new ring, new order, the vector);
+    with commit the vector is written into the oldest slot and order rotated."""
     ring = np.array(ring, dtype=np.float64, copy=True)
     order = list(order)
     if coeffs is not None:
@@ -232,7 +323,11 @@ def advance(ring, order, norm, y=None, coeffs=None):
     else:
         c = [ring[order[k]] for k in range(HIST)]
         dd = _differences(c)
-        base = ((c[7] + dd[1][7]) + dd[2][7]) + dd[3][7]
-        new = base + norm[6] * np.asarray(y, dtype=np.float32).astype(np.float64)
+        base = cubic_base(c[7], dd[1][7], dd[2][7], dd[3][7], horizon, stride)
+        lin = _lin_predict(_regressors(dd, norm), norm, horizon)
+        yv = np.asarray(y, dtype=np.float32).astype(np.float64)
+        new = base + norm[6] * (lin + norm[_beta_row(horizon) + 7] * yv)
+    if not commit:
+        return ring, order, new
     ring[order[0]] = new
     return ring, order[1:] + order[:1], new

@@ -349,19 +349,21 @@ int etics_mlp_to_bf16(const etics_mlp_shape* shape, const float* params, uint16_
     return etics::mlp_to_bf16(shape, params, params_bf16, h.ctx);
 }
 
-int etics_coeff_stats(const double* traj, int T, int D, double* norm, void* stream) {
-    if (!traj || !norm || T < 5 || D < 1 || !aligned(traj, 8) || !aligned(norm, 8))
+int etics_coeff_stats(const double* traj, int T, int D, int stride, double* norm, void* stream) {
+    if (!traj || !norm || T < 5 || D < 1 || stride < 1 || stride > 4 || !aligned(traj, 8) ||
+        !aligned(norm, 8))
         return ETICS_ERR_ARG;
     CtxHolder h;
     const int rc = make_ctx(stream, h);
     if (rc) return rc;
-    return etics::coeff_stats(traj, T, D, norm, h.ctx);
+    return etics::coeff_stats(traj, T, D, stride, norm, h.ctx);
 }
 
 int etics_coeff_features(const double* store, const int32_t* rows, const int32_t* next_rows,
-                         int batch, int D, const double* norm, int layout, uint16_t* x,
+                         int batch, int D, int stride, const double* norm, int layout, uint16_t* x,
                          float* target, void* stream) {
-    if (!store || !rows || !norm || !x || batch < 0 || D < 1 || (next_rows && !target))
+    if (!store || !rows || !norm || !x || batch < 0 || D < 1 || (next_rows && !target) ||
+        stride < 1 || stride > 4)
         return ETICS_ERR_ARG;
     if (layout != ETICS_FEAT_JOINT && layout != ETICS_FEAT_PER_COEFF) return ETICS_ERR_ARG;
     if (!aligned(store, 8) || !aligned(rows, 4) || !aligned(norm, 8) || !aligned(x, 2) ||
@@ -370,14 +372,16 @@ int etics_coeff_features(const double* store, const int32_t* rows, const int32_t
     CtxHolder h;
     const int rc = make_ctx(stream, h);
     if (rc) return rc;
-    return etics::coeff_features(store, rows, next_rows, batch, D, norm,
+    return etics::coeff_features(store, rows, next_rows, batch, D, stride, norm,
                                  layout == ETICS_FEAT_PER_COEFF, x, target, h.ctx);
 }
 
-int etics_coeff_advance(double* ring, int32_t* order, int D, const double* coeffs_in,
-                        const float* y, const double* norm, double* coeffs_out, int commit,
-                        void* stream) {
+int etics_coeff_advance(double* ring, int32_t* order, int D, int stride, int horizon,
+                        const double* coeffs_in, const float* y, int y_stride, const double* norm,
+                        double* coeffs_out, int commit, void* stream) {
     if (!ring || !order || D < 1 || (!coeffs_in == !y) || (y && !norm)) return ETICS_ERR_ARG;
+    if (y && (stride < 1 || stride > 4 || horizon < 1 || horizon > stride || y_stride < 1))
+        return ETICS_ERR_ARG;
     if (!commit && !coeffs_out) return ETICS_ERR_ARG;
     if (!aligned(ring, 8) || !aligned(order, 4) || (coeffs_in && !aligned(coeffs_in, 8)) ||
         (y && !aligned(y, 4)) || (coeffs_out && !aligned(coeffs_out, 8)))
@@ -385,7 +389,8 @@ int etics_coeff_advance(double* ring, int32_t* order, int D, const double* coeff
     CtxHolder h;
     const int rc = make_ctx(stream, h);
     if (rc) return rc;
-    return etics::coeff_advance(ring, order, D, coeffs_in, y, norm, coeffs_out, commit, h.ctx);
+    return etics::coeff_advance(ring, order, D, stride, horizon, coeffs_in, y, y_stride, norm,
+                                coeffs_out, commit, h.ctx);
 }
 
 int etics_force_error(const void* a, const void* r, int64_t N, int precision, double tol_a,

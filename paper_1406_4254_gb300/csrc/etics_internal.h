@@ -97,12 +97,13 @@ int mlp_adam(const etics_mlp_shape* s, float* params, const float* grads, float*
              const LaunchCtx& ctx);
 int mlp_to_bf16(const etics_mlp_shape* s, const float* params, uint16_t* params_bf16,
                 const LaunchCtx& ctx);
-int coeff_stats(const double* traj, int T, int D, double* norm, const LaunchCtx& ctx);
+int coeff_stats(const double* traj, int T, int D, int stride, double* norm, const LaunchCtx& ctx);
 int coeff_features(const double* store, const int32_t* rows, const int32_t* next, int batch, int D,
-                   const double* norm, int per_coeff, uint16_t* x, float* target,
+                   int stride, const double* norm, int per_coeff, uint16_t* x, float* target,
                    const LaunchCtx& ctx);
-int coeff_advance(double* ring, int32_t* order, int D, const double* coeffs_in, const float* y,
-                  const double* norm, double* coeffs_out, int commit, const LaunchCtx& ctx);
+int coeff_advance(double* ring, int32_t* order, int D, int stride, int horizon,
+                  const double* coeffs_in, const float* y, int y_stride, const double* norm,
+                  double* coeffs_out, int commit, const LaunchCtx& ctx);
 int force_error(const void* a, const void* r, int64_t N, int precision, double tol_a,
                 double tol_b, uint64_t* out, const LaunchCtx& ctx);
 

@@ -257,49 +257,24 @@ __global__ void mlp_to_bf16_kernel(const float* __restrict__ p, int64_t n, bf16*
 }
 
 // ---- forecast glue (FP64, single roundings in the written order) -----------
+// A forecast works on a history of eight true coefficient vectors c_0..c_7
+// (oldest first) spaced `stride` steps apart, and predicts the vector k steps
+// after c_7 for each horizon k = 1..stride.  Differences are backward
+// differences along the history (d1_i = c_i - c_{i-1}, ...).
 constexpr int kHist = 8;
+constexpr int kLinFeat = 7;
+constexpr int kMaxStride = 4;
 
 __device__ __forceinline__ bf16 to_bf16(double v) { return __float2bfloat16_rn((float)v); }
 
-constexpr int kNormRows = 7;   // mu, 1/sigma, 1/s1, 1/s2, 1/s3, 1/s4, s4
+// normaliser rows: mu, 1/sigma, 1/s1, 1/s2, 1/s3, 1/s4, s4 (scales of the
+// stride-spaced differences), then per horizon k (from row 7 + 9 (k-1)):
+// the fitted linear predictor beta_k[0..6], the RMS q_k of its residual, 1/q_k
+__host__ __device__ constexpr int norm_rows(int stride) { return 7 + 9 * stride; }
+__host__ __device__ constexpr int norm_beta(int k) { return 7 + 9 * (k - 1); }
 
-// normalisers of a trajectory traj[T][D] (one thread per coefficient): the
-// mean, 1/standard deviation and 1/RMS of the k-th backward differences
-// (k = 1..4), and the RMS s4 itself; a reciprocal of a zero scale is 0
-__global__ void coeff_stats_kernel(const double* __restrict__ traj, int T, int D,
-                                   double* __restrict__ norm) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= D) return;
-    double s = 0.0;
-    for (int t = 0; t < T; ++t) s += traj[(size_t)t * D + j];
-    const double mu = s / T;
-    double v = 0.0, q[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    double prev[4] = {0.0, 0.0, 0.0, 0.0};   // the last difference of each order
-    for (int t = 0; t < T; ++t) {
-        const double c = traj[(size_t)t * D + j];
-        v += (c - mu) * (c - mu);
-        double d = c;
-        for (int k = 0; k < 4 && k < t; ++k) {   // order k + 1 exists from t = k + 1
-            const double nd = d - prev[k];
-            prev[k] = d;
-            d = nd;
-            q[k + 1] += d * d;
-        }
-        if (t < 4) prev[t] = d;
-    }
-    norm[j] = mu;
-    const double sigma = sqrt(v / T);
-    norm[(size_t)D + j] = sigma > 0.0 ? 1.0 / sigma : 0.0;
-    double sk = 0.0;
-    for (int k = 1; k <= 4; ++k) {
-        sk = T > k ? sqrt(q[k] / (T - k)) : 0.0;
-        norm[(size_t)(1 + k) * D + j] = sk > 0.0 ? 1.0 / sk : 0.0;
-    }
-    norm[(size_t)6 * D + j] = sk;
-}
-
-// backward differences of the 8 (or 9) history values: dk[i] = k-th
-// difference ending at c[i], one FP64 subtraction each
+// backward differences of NV values: dk[i] = k-th difference ending at c[i],
+// one FP64 subtraction each
 template <int NV>
 __device__ __forceinline__ void differences(const double (&c)[NV], double (&d1)[NV],
                                             double (&d2)[NV], double (&d3)[NV], double (&d4)[NV]) {
@@ -313,25 +288,222 @@ __device__ __forceinline__ void differences(const double (&c)[NV], double (&d1)[
     for (int i = 4; i < NV; ++i) d4[i] = __dsub_rn(d3[i], d3[i - 1]);
 }
 
+// regressors of a history (differences ending at c_7 over their RMS): the
+// network's feature blocks 1..7 before their bf16 rounding
+__device__ __forceinline__ void lin_regressors(const double (&d1)[kHist], const double (&d2)[kHist],
+                                               const double (&d3)[kHist], const double (&d4)[kHist],
+                                               const double* __restrict__ norm, int D, int j,
+                                               double (&u)[kLinFeat]) {
+    const double is4 = norm[(size_t)5 * D + j];
+    u[0] = __dmul_rn(d1[7], norm[(size_t)2 * D + j]);
+    u[1] = __dmul_rn(d2[7], norm[(size_t)3 * D + j]);
+    u[2] = __dmul_rn(d3[7], norm[(size_t)4 * D + j]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) u[3 + k] = __dmul_rn(d4[7 - k], is4);
+}
+
+// beta_k . u, summed left to right
+__device__ __forceinline__ double lin_predict(const double (&u)[kLinFeat],
+                                              const double* __restrict__ norm, int D, int j, int k) {
+    const double* bk = norm + (size_t)norm_beta(k) * D + j;
+    double s = __dmul_rn(bk[0], u[0]);
+#pragma unroll
+    for (int i = 1; i < kLinFeat; ++i) s = __dadd_rn(s, __dmul_rn(bk[(size_t)i * D], u[i]));
+    return s;
+}
+
+// the cubic through c_4..c_7 evaluated k/stride of a spacing after c_7
+// (Newton's backward form): ((c_7 + s d1_7) + s(s+1)/2 d2_7) + s(s+1)(s+2)/6 d3_7
+__device__ __forceinline__ double cubic_base(double c7, double d1, double d2, double d3, int k,
+                                             int stride) {
+    const double s = __ddiv_rn((double)k, (double)stride);
+    const double a2 = __dmul_rn(__dmul_rn(s, __dadd_rn(s, 1.0)), 0.5);
+    const double a3 = __ddiv_rn(__dmul_rn(a2, __dadd_rn(s, 2.0)), 3.0);
+    return __dadd_rn(__dadd_rn(__dadd_rn(c7, __dmul_rn(s, d1)), __dmul_rn(a2, d2)), __dmul_rn(a3, d3));
+}
+
+// rows 0-6 of a trajectory traj[T][D] (one thread per coefficient): the mean,
+// 1/standard deviation, 1/RMS of the k-th stride-spaced backward differences
+// (k = 1..4, over every t where they exist) and s4; a reciprocal of a zero
+// scale is 0
+__global__ void coeff_stats_kernel(const double* __restrict__ traj, int T, int D, int stride,
+                                   double* __restrict__ norm) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= D) return;
+    double s = 0.0;
+    for (int t = 0; t < T; ++t) s += traj[(size_t)t * D + j];
+    const double mu = s / T;
+    double v = 0.0;
+    for (int t = 0; t < T; ++t) {
+        const double c = traj[(size_t)t * D + j];
+        v += (c - mu) * (c - mu);
+    }
+    double q[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int t = stride; t < T; ++t) {
+        double c[5], d1[5], d2[5], d3[5], d4[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            const int ti = t - (4 - i) * stride;
+            c[i] = ti >= 0 ? traj[(size_t)ti * D + j] : 0.0;
+        }
+        differences<5>(c, d1, d2, d3, d4);
+        q[1] += d1[4] * d1[4];
+        if (t >= 2 * stride) q[2] += d2[4] * d2[4];
+        if (t >= 3 * stride) q[3] += d3[4] * d3[4];
+        if (t >= 4 * stride) q[4] += d4[4] * d4[4];
+    }
+    norm[j] = mu;
+    const double sigma = sqrt(v / T);
+    norm[(size_t)D + j] = sigma > 0.0 ? 1.0 / sigma : 0.0;
+    double sk = 0.0;
+    for (int k = 1; k <= 4; ++k) {
+        const int cnt = T - k * stride;
+        sk = cnt > 0 ? sqrt(q[k] / cnt) : 0.0;
+        norm[(size_t)(1 + k) * D + j] = sk > 0.0 ? 1.0 / sk : 0.0;
+    }
+    norm[(size_t)6 * D + j] = sk;
+}
+
+// history c_0..c_7 ending at trajectory index t (stride apart), its
+// differences and regressors
+__device__ __forceinline__ void traj_history(const double* __restrict__ traj, int D, int j, int t,
+                                             int stride, const double* __restrict__ norm,
+                                             double (&c)[kHist], double (&d1)[kHist],
+                                             double (&d2)[kHist], double (&d3)[kHist],
+                                             double (&u)[kLinFeat]) {
+    double d4[kHist];
+#pragma unroll
+    for (int i = 0; i < kHist; ++i) c[i] = traj[(size_t)(t - (kHist - 1 - i) * stride) * D + j];
+    differences<kHist>(c, d1, d2, d3, d4);
+    lin_regressors(d1, d2, d3, d4, norm, D, j, u);
+}
+
+// the fitted linear predictors of every coefficient (one thread each): over
+// every history of the trajectory with all its horizons inside it (newest
+// index t from 7 stride to T-1-stride), the target of horizon k,
+// t_k = (c_{t+k} - cubic_k) / s4, is regressed by least squares on the
+// regressors u: G beta_k = h_k with G = sum u u^T + lambda tr(G)/7 I
+// (lambda = 1e-12; beta = 0 where G vanishes), solved by Cholesky; q_k = RMS
+// of t_k - beta_k . u over the same histories (q = 1, beta = 0 without any)
+__global__ void coeff_linfit_kernel(const double* __restrict__ traj, int T, int D, int stride,
+                                    double* __restrict__ norm) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= D) return;
+    constexpr int F = kLinFeat;
+    double G[F][F], h[kMaxStride][F];
+#pragma unroll
+    for (int a = 0; a < F; ++a) {
+#pragma unroll
+        for (int k = 0; k < kMaxStride; ++k) h[k][a] = 0.0;
+#pragma unroll
+        for (int b = 0; b < F; ++b) G[a][b] = 0.0;
+    }
+    const double is4 = norm[(size_t)5 * D + j];
+    const int t_lo = (kHist - 1) * stride, t_hi = T - 1 - stride;
+    auto target = [&](const double (&c)[kHist], const double (&d1)[kHist], const double (&d2)[kHist],
+                      const double (&d3)[kHist], int t, int k) -> double {
+        const double base = cubic_base(c[7], d1[7], d2[7], d3[7], k, stride);
+        return __dmul_rn(__dsub_rn(traj[(size_t)(t + k) * D + j], base), is4);
+    };
+    for (int t = t_lo; t <= t_hi; ++t) {
+        double c[kHist], d1[kHist], d2[kHist], d3[kHist], u[F];
+        traj_history(traj, D, j, t, stride, norm, c, d1, d2, d3, u);
+#pragma unroll
+        for (int a = 0; a < F; ++a)
+#pragma unroll
+            for (int b = 0; b <= a; ++b) G[a][b] += u[a] * u[b];
+#pragma unroll
+        for (int k = 0; k < kMaxStride; ++k) {
+            if (k >= stride) break;
+            const double tg = target(c, d1, d2, d3, t, k + 1);
+#pragma unroll
+            for (int a = 0; a < F; ++a) h[k][a] += u[a] * tg;
+        }
+    }
+    double tr = 0.0;
+#pragma unroll
+    for (int a = 0; a < F; ++a) tr += G[a][a];
+    const bool solve = t_hi >= t_lo && tr > 0.0;
+    if (solve) {
+        const double ridge = 1e-12 * tr / F;
+        // Cholesky G = L L^T (lower triangle of G overwritten by L)
+#pragma unroll
+        for (int a = 0; a < F; ++a) {
+            double dsum = G[a][a] + ridge;
+#pragma unroll
+            for (int k = 0; k < a; ++k) dsum -= G[a][k] * G[a][k];
+            const double lkk = sqrt(dsum > 0.0 ? dsum : 0.0);
+            G[a][a] = lkk;
+#pragma unroll
+            for (int b = a + 1; b < F; ++b) {
+                double v = G[b][a];
+#pragma unroll
+                for (int k = 0; k < a; ++k) v -= G[b][k] * G[a][k];
+                G[b][a] = lkk > 0.0 ? v / lkk : 0.0;
+            }
+        }
+    }
+    for (int k = 1; k <= stride; ++k) {
+        double beta[F];
+#pragma unroll
+        for (int a = 0; a < F; ++a) beta[a] = 0.0;
+        if (solve) {
+            double z[F];
+#pragma unroll
+            for (int a = 0; a < F; ++a) {       // L z = h_k
+                double v = h[k - 1][a];
+#pragma unroll
+                for (int i = 0; i < a; ++i) v -= G[a][i] * z[i];
+                z[a] = G[a][a] > 0.0 ? v / G[a][a] : 0.0;
+            }
+#pragma unroll
+            for (int a = F - 1; a >= 0; --a) {  // L^T beta_k = z
+                double v = z[a];
+#pragma unroll
+                for (int i = a + 1; i < F; ++i) v -= G[i][a] * beta[i];
+                beta[a] = G[a][a] > 0.0 ? v / G[a][a] : 0.0;
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < F; ++a) norm[(size_t)(norm_beta(k) + a) * D + j] = beta[a];
+    }
+    for (int k = 1; k <= stride; ++k) {
+        double q = 1.0;
+        if (t_hi >= t_lo) {
+            double ss = 0.0;
+            for (int t = t_lo; t <= t_hi; ++t) {
+                double c[kHist], d1[kHist], d2[kHist], d3[kHist], u[F];
+                traj_history(traj, D, j, t, stride, norm, c, d1, d2, d3, u);
+                const double r = __dsub_rn(target(c, d1, d2, d3, t, k), lin_predict(u, norm, D, j, k));
+                ss += r * r;
+            }
+            q = sqrt(ss / (t_hi - t_lo + 1));
+        }
+        norm[(size_t)(norm_beta(k) + 7) * D + j] = q;
+        norm[(size_t)(norm_beta(k) + 8) * D + j] = q > 0.0 ? 1.0 / q : 0.0;
+    }
+}
+
 // features of the history store[rows[b][0..7]] (oldest first), block blk of
 // coefficient j at x[b][blk * D + j] (joint layout: one row per history) or at
-// x[b * D + j][blk] (per-coefficient layout: one row per coefficient);
-// target[b][j] (the next fourth difference over its RMS) for the next vector
-// store[next[b]]
+// x[b * D + j][blk] (per-coefficient layout: one row per coefficient); with
+// next, the targets of the horizons k = 1..stride (next vectors
+// store[next[b][k-1]]): what the fitted predictor misses, over q_k, at
+// target[(b * D + j) * stride + k-1] (per coefficient) or
+// target[(b * stride + k-1) * D + j] (joint)
 __global__ void coeff_features_kernel(const double* __restrict__ store,
                                       const int32_t* __restrict__ rows,
-                                      const int32_t* __restrict__ next, int B, int D,
+                                      const int32_t* __restrict__ next, int B, int D, int stride,
                                       const double* __restrict__ norm, int per_coeff,
                                       bf16* __restrict__ x, float* __restrict__ target) {
     const int64_t total = (int64_t)B * D;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int b = (int)(i / D), j = (int)(i % D);
-        double c[kHist + 1], d1[kHist + 1], d2[kHist + 1], d3[kHist + 1], d4[kHist + 1];
+        double c[kHist], d1[kHist], d2[kHist], d3[kHist], d4[kHist];
 #pragma unroll
         for (int k = 0; k < kHist; ++k) c[k] = store[(size_t)rows[b * kHist + k] * D + j];
-        c[kHist] = next ? store[(size_t)next[b] * D + j] : 0.0;
-        differences<kHist + 1>(c, d1, d2, d3, d4);
+        differences<kHist>(c, d1, d2, d3, d4);
         const double is4 = norm[(size_t)5 * D + j];
         // element stride between blocks and the position of block 0
         const size_t bs = per_coeff ? 1 : (size_t)D;
@@ -342,15 +514,32 @@ __global__ void coeff_features_kernel(const double* __restrict__ store,
         xr[3 * bs] = to_bf16(__dmul_rn(d3[7], norm[(size_t)4 * D + j]));
 #pragma unroll
         for (int k = 0; k < 4; ++k) xr[(size_t)(4 + k) * bs] = to_bf16(__dmul_rn(d4[7 - k], is4));
-        if (next) target[(size_t)b * D + j] = (float)__dmul_rn(d4[8], is4);
+        if (next) {
+            double u[kLinFeat];
+            lin_regressors(d1, d2, d3, d4, norm, D, j, u);
+            for (int k = 1; k <= stride; ++k) {
+                const double cn = store[(size_t)next[b * stride + k - 1] * D + j];
+                const double tk = __dmul_rn(
+                    __dsub_rn(cn, cubic_base(c[7], d1[7], d2[7], d3[7], k, stride)), is4);
+                const double tau = __dmul_rn(__dsub_rn(tk, lin_predict(u, norm, D, j, k)),
+                                             norm[(size_t)(norm_beta(k) + 8) * D + j]);
+                const size_t o = per_coeff ? (size_t)i * stride + (k - 1)
+                                           : ((size_t)b * stride + (k - 1)) * D + j;
+                target[o] = (float)tau;
+            }
+        }
     }
 }
 
-// the next vector (given, or the cubic extrapolation plus s4 * y); with
-// commit it is written into the oldest ring slot and the slot order rotated;
-// one block
-__global__ void coeff_advance_kernel(double* __restrict__ ring, int32_t* __restrict__ order, int D,
-                                     const double* cin, const float* __restrict__ y,
+// a forecast or a push.  Forecast (y given): the vector k steps after the
+// ring's newest, cubic_k + s4 (beta_k . u + q_k y[j * y_stride]); with
+// commit it is also written into the oldest slot.  Push (cin given): cin is
+// written into the oldest slot.  A write rotates the slot order.  One block.
+constexpr int kAdvanceThreads = 256;
+__global__ void __launch_bounds__(kAdvanceThreads)
+coeff_advance_kernel(double* __restrict__ ring, int32_t* __restrict__ order, int D,
+                                     int stride, int k, const double* cin,
+                                     const float* __restrict__ y, int y_stride,
                                      const double* __restrict__ norm, double* cout, int commit) {
     __shared__ int32_t o[kHist];
     if (threadIdx.x < kHist) o[threadIdx.x] = order[threadIdx.x];
@@ -360,12 +549,16 @@ __global__ void coeff_advance_kernel(double* __restrict__ ring, int32_t* __restr
         if (cin) {
             nv = cin[j];
         } else {
-            double c[kHist], d1[kHist], d2[kHist], d3[kHist], d4[kHist];
+            double c[kHist], d1[kHist], d2[kHist], d3[kHist], d4[kHist], u[kLinFeat];
 #pragma unroll
-            for (int k = 0; k < kHist; ++k) c[k] = ring[(size_t)o[k] * D + j];
+            for (int i = 0; i < kHist; ++i) c[i] = ring[(size_t)o[i] * D + j];
             differences<kHist>(c, d1, d2, d3, d4);
-            const double base = __dadd_rn(__dadd_rn(__dadd_rn(c[7], d1[7]), d2[7]), d3[7]);
-            nv = __dadd_rn(base, __dmul_rn(norm[(size_t)6 * D + j], (double)y[j]));
+            lin_regressors(d1, d2, d3, d4, norm, D, j, u);
+            const double base = cubic_base(c[7], d1[7], d2[7], d3[7], k, stride);
+            const double t4 = __dadd_rn(lin_predict(u, norm, D, j, k),
+                                        __dmul_rn(norm[(size_t)(norm_beta(k) + 7) * D + j],
+                                                  (double)y[(size_t)j * y_stride]));
+            nv = __dadd_rn(base, __dmul_rn(norm[(size_t)6 * D + j], t4));
         }
         if (commit) ring[(size_t)o[0] * D + j] = nv;
         if (cout) cout[j] = nv;
@@ -659,27 +852,31 @@ int mlp_to_bf16(const etics_mlp_shape* s, const float* params, uint16_t* pb, con
     return ETICS_OK;
 }
 
-int coeff_stats(const double* traj, int T, int D, double* norm, const LaunchCtx& ctx) {
-    coeff_stats_kernel<<<(D + 127) / 128, 128, 0, ctx.stream>>>(traj, T, D, norm);
+int coeff_stats(const double* traj, int T, int D, int stride, double* norm, const LaunchCtx& ctx) {
+    coeff_stats_kernel<<<(D + 127) / 128, 128, 0, ctx.stream>>>(traj, T, D, stride, norm);
+    coeff_linfit_kernel<<<(D + 63) / 64, 64, 0, ctx.stream>>>(traj, T, D, stride, norm);
     if (cudaGetLastError()) return ETICS_ERR_CUDA;
-    ++*ctx.launches;
+    *ctx.launches += 2;
     return ETICS_OK;
 }
 
 int coeff_features(const double* store, const int32_t* rows, const int32_t* next, int B, int D,
-                   const double* norm, int per_coeff, uint16_t* x, float* target,
+                   int stride, const double* norm, int per_coeff, uint16_t* x, float* target,
                    const LaunchCtx& ctx) {
     if (B == 0) return ETICS_OK;
     coeff_features_kernel<<<grid_1d((int64_t)B * D, ctx), 256, 0, ctx.stream>>>(
-        store, rows, next, B, D, norm, per_coeff, reinterpret_cast<bf16*>(x), target);
+        store, rows, next, B, D, stride, norm, per_coeff, reinterpret_cast<bf16*>(x), target);
     if (cudaGetLastError()) return ETICS_ERR_CUDA;
     ++*ctx.launches;
     return ETICS_OK;
 }
 
-int coeff_advance(double* ring, int32_t* order, int D, const double* cin, const float* y,
-                  const double* norm, double* cout, int commit, const LaunchCtx& ctx) {
-    coeff_advance_kernel<<<1, 1024, 0, ctx.stream>>>(ring, order, D, cin, y, norm, cout, commit);
+int coeff_advance(double* ring, int32_t* order, int D, int stride, int horizon, const double* cin,
+                  const float* y, int y_stride, const double* norm, double* cout, int commit,
+                  const LaunchCtx& ctx) {
+    coeff_advance_kernel<<<1, kAdvanceThreads, 0, ctx.stream>>>(ring, order, D, stride, horizon,
+                                                                 cin, y, y_stride, norm, cout,
+                                                                 commit);
     if (cudaGetLastError()) return ETICS_ERR_CUDA;
     ++*ctx.launches;
     return ETICS_OK;

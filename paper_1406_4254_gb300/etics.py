@@ -97,9 +97,9 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         flt = ctypes.c_float
         lib.etics_mlp_adam.argtypes = [mp, vp, vp, vp, vp, i64, flt, flt, flt, flt, vp, vp]
         lib.etics_mlp_to_bf16.argtypes = [mp, vp, vp, vp]
-        lib.etics_coeff_stats.argtypes = [vp, i32, i32, vp, vp]
-        lib.etics_coeff_features.argtypes = [vp, vp, vp, i32, i32, vp, i32, vp, vp, vp]
-        lib.etics_coeff_advance.argtypes = [vp, vp, i32, vp, vp, vp, vp, i32, vp]
+        lib.etics_coeff_stats.argtypes = [vp, i32, i32, i32, vp, vp]
+        lib.etics_coeff_features.argtypes = [vp, vp, vp, i32, i32, i32, vp, i32, vp, vp, vp]
+        lib.etics_coeff_advance.argtypes = [vp, vp, i32, i32, i32, vp, vp, i32, vp, vp, i32, vp]
         lib.etics_force_error.argtypes = [vp, vp, i64, i32, dbl, dbl, vp, vp]
         lib.etics_get_error.argtypes = [vp]
         lib.etics_strerror.argtypes = [i32]
@@ -410,45 +410,58 @@ def mlp_to_bf16(dims, params, params_bf16, stream=None) -> None:
                                     params_bf16.data_ptr(), _stream(stream)), "etics_mlp_to_bf16")
 
 
-def coeff_stats(traj: torch.Tensor, norm: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """(7, D) normalisers of a (T, D) float64 coefficient trajectory."""
+def norm_rows(stride: int) -> int:
+    """Rows of the forecasting normalisers for histories of this stride."""
+    return 7 + 9 * int(stride)
+
+
+def coeff_stats(traj: torch.Tensor, stride: int = 1, norm: torch.Tensor | None = None,
+                stream=None) -> torch.Tensor:
+    """(7 + 9 stride, D) normalisers of a (T, D) float64 coefficient
+    trajectory: scales of the state and of its differences at spacing
+    ``stride``, then per horizon k = 1..stride the fitted linear predictor and
+    the RMS of its residual."""
     _vector(traj, torch.float64, None, "traj")
     t, d = traj.shape
+    rows = norm_rows(stride)
     if norm is None:
-        norm = torch.empty((NORM_ROWS, d), dtype=torch.float64, device=traj.device)
-    _vector(norm, torch.float64, NORM_ROWS * d, "norm")
-    _check(load().etics_coeff_stats(traj.data_ptr(), t, d, norm.data_ptr(), _stream(stream)),
-           "etics_coeff_stats")
+        norm = torch.empty((rows, d), dtype=torch.float64, device=traj.device)
+    _vector(norm, torch.float64, rows * d, "norm")
+    _check(load().etics_coeff_stats(traj.data_ptr(), t, d, int(stride), norm.data_ptr(),
+                                    _stream(stream)), "etics_coeff_stats")
     return norm
 
 
 FEAT_JOINT, FEAT_PER_COEFF = 0, 1
-NORM_ROWS = 7
 
 
 def coeff_features(store: torch.Tensor, rows: torch.Tensor, norm: torch.Tensor,
                    next_rows: torch.Tensor | None = None, x: torch.Tensor | None = None,
-                   target: torch.Tensor | None = None, per_coeff: bool = False, stream=None):
+                   target: torch.Tensor | None = None, per_coeff: bool = False, stride: int = 1,
+                   stream=None):
     """Network inputs of the histories store[rows] (rows: (batch, 8) int32,
     oldest first): (batch, 8D) bfloat16 in the joint layout, (batch*D, 8) per
-    coefficient; with next_rows also the targets (batch, D) float32."""
+    coefficient; with next_rows ((batch, stride) int32: the vectors 1..stride
+    steps after each history) also the targets, float32 (batch*D, stride) per
+    coefficient or (batch, stride*D) jointly."""
     _vector(store, torch.float64, None, "store")
     _vector(rows, torch.int32, None, "rows")
     d = store.shape[1]
     b = rows.shape[0]
-    _vector(norm, torch.float64, NORM_ROWS * d, "norm")
+    _vector(norm, torch.float64, norm_rows(stride) * d, "norm")
     if x is None:
         shape = (b * d, 8) if per_coeff else (b, 8 * d)
         x = torch.empty(shape, dtype=torch.bfloat16, device=store.device)
     _vector(x, torch.bfloat16, b * 8 * d, "x")
     np_ = tp = None
     if next_rows is not None:
-        _vector(next_rows, torch.int32, b, "next_rows")
+        _vector(next_rows, torch.int32, b * stride, "next_rows")
         if target is None:
-            target = torch.empty((b, d), dtype=torch.float32, device=store.device)
-        _vector(target, torch.float32, b * d, "target")
+            shape = (b * d, stride) if per_coeff else (b, stride * d)
+            target = torch.empty(shape, dtype=torch.float32, device=store.device)
+        _vector(target, torch.float32, b * d * stride, "target")
         np_, tp = next_rows.data_ptr(), target.data_ptr()
-    _check(load().etics_coeff_features(store.data_ptr(), rows.data_ptr(), np_, b, d,
+    _check(load().etics_coeff_features(store.data_ptr(), rows.data_ptr(), np_, b, d, int(stride),
                                        norm.data_ptr(), FEAT_PER_COEFF if per_coeff else FEAT_JOINT,
                                        x.data_ptr(), tp, _stream(stream)),
            "etics_coeff_features")
@@ -457,13 +470,17 @@ def coeff_features(store: torch.Tensor, rows: torch.Tensor, norm: torch.Tensor,
 
 def coeff_advance(ring: torch.Tensor, order: torch.Tensor, norm: torch.Tensor | None = None,
                   coeffs_in: torch.Tensor | None = None, y: torch.Tensor | None = None,
-                  coeffs_out: torch.Tensor | None = None, commit: bool = True,
-                  stream=None) -> None:
+                  coeffs_out: torch.Tensor | None = None, commit: bool = True, stride: int = 1,
+                  horizon: int = 1, y_stride: int = 1, stream=None) -> None:
+    """Forecast at ``horizon`` from the ring (y: one network output per
+    coefficient, y[j * y_stride]) or push coeffs_in; commit writes the vector
+    into the oldest slot and rotates ``order``."""
     _vector(ring, torch.float64, None, "ring")
     _vector(order, torch.int32, 8, "order")
     d = ring.shape[1]
     ptr = lambda t: t.data_ptr() if t is not None else None  # noqa: E731
-    _check(load().etics_coeff_advance(ring.data_ptr(), order.data_ptr(), d, ptr(coeffs_in), ptr(y),
+    _check(load().etics_coeff_advance(ring.data_ptr(), order.data_ptr(), d, int(stride),
+                                      int(horizon), ptr(coeffs_in), ptr(y), int(y_stride),
                                       ptr(norm), ptr(coeffs_out), int(bool(commit)),
                                       _stream(stream)), "etics_coeff_advance")
 

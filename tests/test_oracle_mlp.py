@@ -148,7 +148,7 @@ def test_stats_closed_form():
     a = np.array([1.0, -2.0, 0.5])
     b = np.array([0.25, 0.0, -3.0])
     norm = mlp.stats(_poly_store(0, T, [a, b]))
-    assert norm.shape == (mlp.NORM_ROWS, 3)
+    assert norm.shape == (mlp.norm_rows(1), 3)
     np.testing.assert_allclose(norm[0], a + b * (T - 1) / 2, rtol=1e-15)
     sig = np.abs(b) * np.sqrt((T * T - 1) / 12.0)
     np.testing.assert_allclose(norm[1], np.where(sig > 0, 1 / np.where(sig > 0, sig, 1), 0), rtol=1e-14)
@@ -164,8 +164,12 @@ def test_stats_of_a_cubic():
     assert np.all(norm[5] == 0) and np.all(norm[6] == 0)
 
 
-def _norm(d, mu=0.5, isg=2.0, is1=4.0, is2=16.0, is3=0.5, is4=8.0, s4=0.125):
-    return np.array([[v] * d for v in (mu, isg, is1, is2, is3, is4, s4)], dtype=np.float64)
+def _norm(d, mu=0.5, isg=2.0, is1=4.0, is2=16.0, is3=0.5, is4=8.0, s4=0.125,
+          beta=(0.0,) * 7, q=1.0):
+    """Normaliser rows by hand; beta = 0 and q = 1 leave the cubic base and the
+    plain next-fourth-difference target."""
+    vals = (mu, isg, is1, is2, is3, is4, s4) + tuple(beta) + (q, 1.0 / q if q else 0.0)
+    return np.array([[v] * d for v in vals], dtype=np.float64)
 
 
 def test_features_of_cubic_history():
@@ -240,3 +244,127 @@ def test_advance_inverts_target():
     # pushing a given vector writes it into the oldest slot
     ring3, order3, _ = mlp.advance(ring2, order2, norm, coeffs=np.array([7.0, 8.0, 9.0]))
     assert order3 == [2, 3, 4, 5, 6, 7, 0, 1] and np.array_equal(ring3[1], [7.0, 8.0, 9.0])
+
+
+def _windows(traj, norm):
+    """Regressors and targets of every 9-vector window, from numpy's
+    difference operator (independent of the oracle's difference lists)."""
+    U, t = [], []
+    for w in range(traj.shape[0] - 8):
+        c = traj[w:w + 9]
+        d1, d2, d3, d4 = (np.diff(c, n=k, axis=0) for k in (1, 2, 3, 4))
+        # the history ends at c[7]: its k-th difference is the second-to-last
+        u = [d1[-2] * norm[2], d2[-2] * norm[3], d3[-2] * norm[4],
+             d4[-2] * norm[5], d4[-3] * norm[5], d4[-4] * norm[5], d4[-5] * norm[5]]
+        U.append(np.stack(u))
+        t.append(d4[-1] * norm[5])
+    return np.stack(U), np.stack(t)
+
+
+def test_linear_fit_is_the_least_squares_solution():
+    # a smooth trajectory with noise: the fitted beta satisfies the ridged
+    # normal equations of the windows' regressors, and moving beta in any
+    # direction raises the residual sum of squares
+    rng = np.random.default_rng(21)
+    T, D = 70, 4
+    ts = np.arange(T)[:, None]
+    traj = (np.cos(0.3 * ts * rng.uniform(0.5, 1.5, size=(1, D))) + 1e-3 * ts
+            + 1e-4 * rng.normal(size=(T, D)))
+    norm = mlp.stats(traj)
+    assert norm.shape == (mlp.norm_rows(1), D)
+    U, t = _windows(traj, norm)
+    for j in range(D):
+        A, b, beta = U[:, :, j], t[:, j], norm[7:14, j]
+        G = A.T @ A
+        lhs = (G + mlp.RIDGE * np.trace(G) / 7 * np.eye(7)) @ beta
+        np.testing.assert_allclose(lhs, A.T @ b, rtol=1e-7, atol=1e-9 * np.abs(A.T @ b).max())
+        rss = np.sum((b - A @ beta) ** 2)
+        assert norm[14, j] == pytest.approx(np.sqrt(rss / len(b)), rel=1e-9)
+        for k in range(7):
+            step = np.zeros(7)
+            step[k] = 1e-3 * max(1.0, abs(beta[k]))
+            assert np.sum((b - A @ (beta + step)) ** 2) > rss
+            assert np.sum((b - A @ (beta - step)) ** 2) > rss
+
+
+def test_linear_fit_predicts_a_sinusoid_exactly():
+    # the fourth differences of cos(w t) obey d4_{t+1} = 2 cos(w) d4_t - d4_{t-1}:
+    # a linear function of the regressors, so the fitted predictor's residual
+    # vanishes and the forecast with y = 0 is the next value (which the cubic
+    # base alone misses)
+    w = np.array([0.7, 1.3, 2.1])
+    T = 40
+    traj = np.cos(np.arange(T)[:, None] * w[None, :])
+    norm = mlp.stats(traj)
+    assert np.all(norm[14] < 1e-6)
+    ring = traj[20:28].copy()
+    _, _, new = mlp.advance(ring, list(range(8)), norm, y=np.zeros(3))
+    np.testing.assert_allclose(new, traj[28], atol=1e-9)
+    cubic = 4 * traj[27] - 6 * traj[26] + 4 * traj[25] - traj[24]
+    assert np.all(np.abs(cubic - traj[28]) > 1e-3)
+
+
+def test_linear_fit_degenerate_cases():
+    # a constant coefficient and a trajectory too short for a window
+    traj = np.stack([np.full(12, 1.5), np.arange(12, dtype=np.float64) ** 2], axis=1)
+    norm = mlp.stats(traj)
+    assert np.all(norm[7:14, 0] == 0) and norm[14, 0] == 0 and norm[15, 0] == 0
+    short = mlp.stats(traj[:8])
+    assert np.all(short[7:14] == 0) and np.all(short[14] == 1) and np.all(short[15] == 1)
+
+
+def test_cubic_base_interpolates_a_cubic_at_every_horizon():
+    # a cubic trajectory sampled at stride 3: the base at s = k/3 is the
+    # polynomial's value k steps after the newest sample
+    coef = [np.array([0.5, -1.0]), np.array([0.25, 0.125]), np.array([-0.0625, 0.03125]),
+            np.array([0.0078125, -0.00390625])]
+    store = _poly_store(0, 40, coef)
+    hist = [store[5 + 3 * i] for i in range(8)]        # t = 5, 8, ..., 26
+    dd = mlp._differences(hist)
+    for k in (1, 2, 3):
+        p = mlp.cubic_base(hist[7], dd[1][7], dd[2][7], dd[3][7], k, 3)
+        np.testing.assert_allclose(p, store[26 + k], rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("stride", [2, 3, 4])
+def test_strided_fit_predicts_a_sinusoid_at_every_horizon(stride):
+    # cos(w t) sampled at any stride spans two dimensions, so every horizon's
+    # next value is a linear function of the history: the fitted predictors
+    # are exact, and the forecast with y = 0 reproduces the trajectory
+    w = np.array([0.31, 0.57, 0.83])
+    T = 12 * stride + 40
+    traj = np.cos(np.arange(T)[:, None] * w[None, :])
+    norm = mlp.stats(traj, stride=stride)
+    assert norm.shape == (mlp.norm_rows(stride), 3)
+    for k in range(1, stride + 1):
+        assert np.all(norm[mlp._beta_row(k) + 7] < 1e-6), k
+    t7 = 10 * stride
+    ring = np.stack([traj[t7 - (7 - i) * stride] for i in range(8)])
+    for k in range(1, stride + 1):
+        _, _, new = mlp.advance(ring, list(range(8)), norm, y=np.zeros(3), stride=stride,
+                                horizon=k, commit=False)
+        np.testing.assert_allclose(new, traj[t7 + k], atol=1e-8)
+
+
+def test_strided_targets_and_forecast_invert():
+    # the features' target of horizon k and the forecast with y = target give
+    # back the trajectory's vector k steps ahead (to rounding)
+    rng = np.random.default_rng(23)
+    stride, T, D = 3, 60, 5
+    ts = np.arange(T)[:, None]
+    traj = np.sin(0.2 * ts * rng.uniform(0.5, 1.5, size=(1, D))) + 1e-3 * rng.normal(size=(T, D))
+    norm = mlp.stats(traj, stride=stride)
+    t7 = 30
+    rows = np.array([[t7 - (7 - i) * stride for i in range(8)]])
+    nxt = np.array([[t7 + 1, t7 + 2, t7 + 3]])
+    _, tg = mlp.features(traj, rows, norm, next_rows=nxt, per_coeff=True, stride=stride)
+    assert tg.shape == (D, stride)
+    _, tj = mlp.features(traj, rows, norm, next_rows=nxt, per_coeff=False, stride=stride)
+    assert tj.shape == (1, stride * D)
+    np.testing.assert_array_equal(tj.reshape(stride, D).T, tg)
+    ring = traj[rows[0]]
+    for k in range(1, stride + 1):
+        _, _, new = mlp.advance(ring, list(range(8)), norm, y=tg[:, k - 1], stride=stride,
+                                horizon=k, commit=False)
+        scale = np.abs(norm[6] * norm[mlp._beta_row(k) + 7]).max()
+        np.testing.assert_allclose(new, traj[t7 + k], atol=1e-6 * scale + 1e-15)

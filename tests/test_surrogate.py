@@ -120,56 +120,75 @@ def _traj(T, D, seed):
             + rng.normal(size=(1, D)) * 1e-4 * t * t + rng.normal(size=(T, D)) * 1e-6)
 
 
-def test_stats_match_oracle():
+@pytest.mark.parametrize("stride", [1, 3])
+def test_stats_match_oracle(stride):
     traj = _traj(50, 77, 9)
     traj[:, 5] = 1.25                             # a constant coefficient: zero scales
-    norm = etics.coeff_stats(torch.tensor(traj, device="cuda")).cpu().numpy()
-    ref = omlp.stats(traj)
-    np.testing.assert_allclose(norm, ref, rtol=1e-12, atol=1e-300)
+    norm = etics.coeff_stats(torch.tensor(traj, device="cuda"), stride).cpu().numpy()
+    ref = omlp.stats(traj, stride=stride)
+    assert norm.shape == ref.shape == (omlp.norm_rows(stride), 77)
+    np.testing.assert_allclose(norm[:7], ref[:7], rtol=1e-12, atol=1e-300)
+    # the fitted predictors: the GPU's Cholesky against the oracle's LU solve
+    # of the same normal equations (Gram matrices of differences are
+    # ill-conditioned), then the residual RMS they imply
+    for k in range(1, stride + 1):
+        b = omlp._beta_row(k)
+        scale = np.abs(ref[b:b + 7]).max(axis=0) + 1e-300
+        assert np.all(np.abs(norm[b:b + 7] - ref[b:b + 7]) <= 1e-6 * scale), k
+        np.testing.assert_allclose(norm[b + 7], ref[b + 7], rtol=1e-6)
     assert np.all(norm[1:, 5] == 0)
 
 
-@pytest.mark.parametrize("per_coeff", [False, True])
-def test_features_bit_exact(per_coeff):
-    traj = _traj(40, 131, 10)
-    norm = omlp.stats(traj)
+@pytest.mark.parametrize("per_coeff,stride", [(False, 1), (True, 1), (False, 3), (True, 3)])
+def test_features_bit_exact(per_coeff, stride):
+    traj = _traj(60, 131, 10)
+    norm = omlp.stats(traj, stride=stride)
     rng = np.random.default_rng(11)
-    last = rng.integers(7, 39, size=23)
-    rows = last[:, None] + np.arange(-7, 1)[None, :]
+    last = rng.integers(7 * stride, 59 - stride, size=23)
+    rows = last[:, None] + stride * np.arange(-7, 1)[None, :]
     rows[3] = rows[3][::-1]                       # any slot order is allowed
+    nxt = last[:, None] + np.arange(1, stride + 1)[None, :]
     x, tg = etics.coeff_features(torch.tensor(traj, device="cuda"),
                                  torch.tensor(rows, dtype=torch.int32, device="cuda"),
                                  torch.tensor(norm, device="cuda"),
-                                 torch.tensor(last + 1, dtype=torch.int32, device="cuda"),
-                                 per_coeff=per_coeff)
-    xr, tr = omlp.features(traj, rows, norm, next_rows=last + 1, per_coeff=per_coeff)
+                                 torch.tensor(nxt, dtype=torch.int32, device="cuda"),
+                                 per_coeff=per_coeff, stride=stride)
+    xr, tr = omlp.features(traj, rows, norm, next_rows=nxt, per_coeff=per_coeff, stride=stride)
     assert np.array_equal(_bits(x).reshape(xr.shape), xr)
+    assert tg.shape == tr.shape
     assert np.array_equal(tg.cpu().numpy(), tr)
 
 
-def test_advance_bit_exact_and_ring_order():
+@pytest.mark.parametrize("stride", [1, 3])
+def test_advance_bit_exact_and_ring_order(stride):
     D = 53
-    traj = _traj(12, D, 12)
-    nr = omlp.stats(traj)
+    traj = _traj(40, D, 12)
+    nr = omlp.stats(traj, stride=stride)
     norm = torch.tensor(nr, device="cuda")
-    ring = torch.tensor(traj[:8], device="cuda")
+    ring0 = traj[:8 * stride:stride]
+    ring = torch.tensor(ring0, device="cuda")
     start = [3, 4, 5, 6, 7, 0, 1, 2]
     order = torch.tensor(start, dtype=torch.int32, device="cuda")
-    y = np.random.default_rng(13).normal(size=D).astype(np.float32)
+    y = np.random.default_rng(13).normal(size=(D, stride)).astype(np.float32)
+    yd = torch.tensor(y, device="cuda")
     out = torch.empty(D, dtype=torch.float64, device="cuda")
-    # a dry forecast changes nothing
-    etics.coeff_advance(ring, order, norm, y=torch.tensor(y, device="cuda"), coeffs_out=out,
-                        commit=False)
-    r_ring, r_order, r_new = omlp.advance(traj[:8], start, nr, y=y)
-    assert np.array_equal(out.cpu().numpy(), r_new)
-    assert np.array_equal(ring.cpu().numpy(), traj[:8])
-    assert order.cpu().tolist() == start
-    # committed forecast, then a pushed vector
-    etics.coeff_advance(ring, order, norm, y=torch.tensor(y, device="cuda"), coeffs_out=out)
+    # forecasts at every horizon change nothing; y read with its stride
+    for k in range(1, stride + 1):
+        etics.coeff_advance(ring, order, norm, y=yd.view(-1)[k - 1:], coeffs_out=out,
+                            commit=False, stride=stride, horizon=k, y_stride=stride)
+        _, _, r_new = omlp.advance(ring0, start, nr, y=y[:, k - 1], stride=stride, horizon=k,
+                                   commit=False)
+        assert np.array_equal(out.cpu().numpy(), r_new), k
+        assert np.array_equal(ring.cpu().numpy(), ring0)
+        assert order.cpu().tolist() == start
+    # a committed forecast, then a pushed vector
+    etics.coeff_advance(ring, order, norm, y=yd.view(-1), coeffs_out=out, stride=stride,
+                        horizon=1, y_stride=stride)
+    r_ring, r_order, _ = omlp.advance(ring0, start, nr, y=y[:, 0], stride=stride, horizon=1)
     assert np.array_equal(ring.cpu().numpy(), r_ring) and order.cpu().tolist() == r_order
-    push = torch.tensor(traj[9], device="cuda")
+    push = torch.tensor(traj[39], device="cuda")
     etics.coeff_advance(ring, order, coeffs_in=push)
-    r_ring, r_order, _ = omlp.advance(r_ring, r_order, nr, coeffs=traj[9])
+    r_ring, r_order, _ = omlp.advance(r_ring, r_order, nr, coeffs=traj[39])
     assert np.array_equal(ring.cpu().numpy(), r_ring) and order.cpu().tolist() == r_order
 
 
@@ -213,31 +232,74 @@ def test_leapfrog_step_coeffs_equals_plain_step():
 
 # ---- end to end: the forecast's gain over plain reuse ------------------------
 def test_forecast_beats_coefficient_reuse():
-    n_max, l_max = 6, 4
+    n_max, l_max, S = 6, 4, 3
     pm, vel = inputs.hernquist_bar(1 << 14, seed=16, eps=0.05)
     x = torch.tensor(pm, dtype=torch.float32, device="cuda")
     v = torch.zeros_like(x)
     v[:, :3] = torch.tensor(vel, dtype=torch.float32)
     dt = 0.005
-    traj, acc = surrogate.coefficient_trajectory(x, v, 160, dt, n_max, l_max)
-    fc = surrogate.Forecaster(n_max, l_max, hidden=64, seed=17)
-    losses = fc.fit(traj[:121], iters=400, batch=16, lr=2e-3, seed=18, log_every=100)
-    assert losses[-1] < losses[0]
-    hold, lin, cubic, net = fc.one_step_errors(traj, 120)
-    assert np.median(hold) == pytest.approx(1.0)
-    # the forecast beats plain reuse by orders of magnitude and the trained
-    # correction does not lose against its cubic base
-    assert np.median(net) < 1e-2 * np.median(hold)
-    assert np.median(net) <= 1.05 * np.median(cubic)
-    # rollout: 3 of 4 steps forecast, every 4th judged by plain SCF
-    state = (x.clone(), v.clone(), acc.clone())
-    fc.reset(traj)
-    st_f = surrogate.run(*state, 40, dt, fc, period=4, tol_med=1e-3, tol_p99=1e-2)
-    state = (x.clone(), v.clone(), acc.clone())
-    fc.reset(traj)
-    st_h = surrogate.run(*state, 40, dt, fc, period=4, tol_med=1e-3, tol_p99=1e-2, mode="hold")
+    traj, acc = surrogate.coefficient_trajectory(x, v, 200, dt, n_max, l_max)
+    fc = surrogate.Forecaster(n_max, l_max, stride=S, hidden=64, seed=17)
+    losses = fc.fit(traj[:161], iters=400, batch=16, lr=2e-3, seed=18, log_every=100)
+    # the network's target is what the fitted predictors miss, normalised to
+    # unit RMS; its minibatch loss stays of order 1 rather than falling
+    assert all(np.isfinite(losses)) and max(losses) < 3.0
+    he = fc.horizon_errors(traj, 160)
+    for k in range(1, S + 1):
+        med = {n: np.median(a) for n, a in he[k].items()}
+        # forecasts beat holding the last vector by orders of magnitude and
+        # the fitted predictor beats its cubic base; the network, trained on
+        # 161 vectors of a small system, may overfit a little
+        assert med["net"] < 1e-2 * med["hold"], (k, med)
+        assert med["fitted"] < med["cubic"], (k, med)
+        assert med["net"] <= 1.5 * med["fitted"], (k, med)
+    # rollout with a recomputation every third step, judged by plain SCF.
+    # The force error of any forecast grows with the particle noise of the
+    # coefficients (~N^-1/2); the stated budget is met at 2^26 particles
+    # (test_forecast_meets_the_stated_budget), so this 2^14 system is judged
+    # at a budget 100 times looser: the forecast passes checks that plain
+    # reuse fails, so it forecasts more steps, and its errors at the checks
+    # are smaller
+    runs = {}
+    for mode in ("forecast", "hold"):
+        state = (x.clone(), v.clone(), acc.clone())
+        fc.reset(traj)
+        runs[mode] = surrogate.run(*state, 42, dt, fc, mode=mode, tol_med=1e-3, tol_p99=1e-2)
     etics.check_error()
-    assert st_f.recomputes + st_f.forecasts == 40
-    mf = np.median([c[3] for c in st_f.checks[1:]])
-    mh = np.median([c[3] for c in st_h.checks[1:]])
+    st_f, st_h = runs["forecast"], runs["hold"]
+    assert st_f.recomputes + st_f.forecasts == 42
+    assert st_f.forecasts >= st_h.forecasts + 6, (st_f.forecasts, st_h.forecasts)
+    mf = np.median([c[3] for c in st_f.checks])
+    mh = np.median([c[3] for c in st_h.checks])
     assert mf < 0.5 * mh, (mf, mh)
+
+
+def test_forecast_meets_the_stated_budget():
+    # the experiment's system (Hernquist + 5% bar, 2^26 particles, SCF (14, 8),
+    # dt = 0.005) on a shorter trajectory: with a recomputation every third
+    # step the forecast meets the stated budget (median <= 1e-5, 99th
+    # percentile <= 1e-4 on 4096 particles) at most checks, plain reuse at
+    # almost none
+    n_max, l_max, S, dt = 14, 8, 3, 0.005
+    pm, vel = inputs.hernquist_bar(1 << 26, seed=0, eps=0.05)
+    x = torch.tensor(pm, dtype=torch.float32, device="cuda")
+    v = torch.zeros_like(x)
+    v[:, :3] = torch.tensor(vel, dtype=torch.float32, device="cuda")
+    del pm, vel
+    traj, acc = surrogate.coefficient_trajectory(x, v, 500, dt, n_max, l_max)
+    fc = surrogate.Forecaster(n_max, l_max, stride=S, hidden=256, seed=0)
+    fc.fit(traj, iters=1000, batch=16, lr=1e-3, seed=0)
+    runs = {}
+    for mode in ("forecast", "hold"):
+        state = (x.clone(), v.clone(), acc.clone())
+        fc.reset(traj)
+        runs[mode] = surrogate.run(*state, 60, dt, fc, mode=mode)
+        del state
+    etics.check_error()
+    st_f, st_h = runs["forecast"], runs["hold"]
+    passed_f = len(st_f.checks) - st_f.fallbacks
+    passed_h = len(st_h.checks) - st_h.fallbacks
+    assert len(st_f.checks) == 20
+    assert passed_f >= 14, st_f.checks
+    assert passed_h <= 2, st_h.checks
+    assert st_f.forecasts >= 28, st_f.forecasts
