@@ -395,40 +395,63 @@ mex_pass1_kernel(const Vec4<R>* __restrict__ posm, const uint32_t* __restrict__ 
 
 // ---------------------------------------------------------------------------
 // carry: exclusive scans of the tile sums over tiles, one block per
-// component; forward for inner moments, reverse for outer (fixed order)
+// component; forward for inner moments, reverse for outer (fixed order).
+// FP64 arithmetic is slow on this GPU (about 1/76 of the FP32 rate), so the scan
+// keeps the FP64 additions per block near the minimum: thread t owns a
+// contiguous run of scan positions, adds them in order, the run totals are
+// scanned by one warp-shuffle scan per warp and one over the warp totals,
+// then each thread writes its positions' exclusive sums.  Every addition
+// order depends only on (ntiles, ncomp): deterministic.
 // ---------------------------------------------------------------------------
-constexpr int kCarryThreads = 1024;
+constexpr int kCarryThreads = 256;
+constexpr int kCarryWarps = kCarryThreads / 32;
 static __global__ void __launch_bounds__(kCarryThreads)
 mex_carry_kernel(const double* __restrict__ tile_agg, int ntiles, int ncomp,
                  double* __restrict__ carry) {
-    __shared__ double s_w[kCarryThreads / 32];
-    pdl_wait();
+    __shared__ double s_w[kCarryWarps];
+    pdl_wait();   // the tile sums come from pass 1
     const int c = blockIdx.x;
     const bool rev = c >= ncomp;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int chunk = (ntiles + kCarryThreads - 1) / kCarryThreads;
     const int o0 = tid * chunk;
-    auto tile_of = [&](int o) { return rev ? ntiles - 1 - o : o; };
+    const int o1 = o0 + chunk < ntiles ? o0 + chunk : ntiles;
+    const size_t stride = (size_t)2 * ncomp;
+    auto at = [&](int o) { return (size_t)(rev ? ntiles - 1 - o : o) * stride + c; };
+    // this thread's run, in scan order (read coherently after the wait)
     double local = 0.0;
-    for (int o = o0; o < o0 + chunk && o < ntiles; ++o)
-        local += tile_agg[(size_t)tile_of(o) * 2 * ncomp + c];
+#pragma unroll 4
+    for (int o = o0; o < o1; ++o) local += __ldcg(tile_agg + at(o));
+    // inclusive scan of the run totals over the warp
     double x = local;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const double t = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += t;
+    for (int d = 1; d < 32; d <<= 1) {
+        const double t = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += t;
     }
-    if (lane == 31) s_w[warp] = x;
-    __syncthreads();
-    double run = 0.0;
-    for (int w = 0; w < warp; ++w) run += s_w[w];
     double ex = __shfl_up_sync(0xffffffffu, x, 1);
     if (lane == 0) ex = 0.0;
-    run += ex;
-    for (int o = o0; o < o0 + chunk && o < ntiles; ++o) {
-        const size_t idx = (size_t)tile_of(o) * 2 * ncomp + c;
-        carry[idx] = run;
-        run += tile_agg[idx];
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        // exclusive scan of the warp totals, in warp order
+        double w = lane < kCarryWarps ? s_w[lane] : 0.0;
+#pragma unroll
+        for (int d = 1; d < kCarryWarps; d <<= 1) {
+            const double t = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= d) w += t;
+        }
+        double we = __shfl_up_sync(0xffffffffu, w, 1);
+        if (lane == 0) we = 0.0;
+        __syncwarp();
+        if (lane < kCarryWarps) s_w[lane] = we;
+    }
+    __syncthreads();
+    double run = warp == 0 ? ex : s_w[warp] + ex;
+    for (int o = o0; o < o1; ++o) {
+        const size_t i = at(o);
+        carry[i] = run;
+        run += __ldcg(tile_agg + i);
     }
 }
 

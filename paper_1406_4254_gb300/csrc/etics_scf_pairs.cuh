@@ -97,7 +97,7 @@ static __constant__ PairPlan<LM, CAP> c_pair_plan = make_pair_plan<LM, CAP>();
 struct ScfPairParams {
     const float4* posm;
     int64_t N;
-    int ntiles;
+    int64_t per;       // particles per block (even): block b takes [b*per, (b+1)*per)
     double* partial;   // [gridDim.x][nbins][NR][CAP]
     unsigned* err;
 };
@@ -135,17 +135,17 @@ __device__ __forceinline__ void pair_steps(float2 (&acc)[NR][CAP], const float2 
     }
 }
 
-// phase 2 for bin B over one tile
+// phase 2 for bin B over the first `np` particle pairs of one tile
 template <int NR, int LM, int CAP, int B>
 __device__ __forceinline__ void pair_bin_tile(float2 (&acc)[NR][CAP], const float* H,
-                                              const float* xs, int lane) {
+                                              const float* xs, int lane, int np) {
     constexpr PairBin bd = PairConst<LM, CAP>::plan.bin[B];
     constexpr int NC = bd.nc;
     constexpr int col0 = bd.l * bd.l + bd.c0;
     const float2* H2 = reinterpret_cast<const float2*>(H);
     const float2* x2 = reinterpret_cast<const float2*>(xs);
 #pragma unroll 1
-    for (int p = lane; p < kPairTile / 2; p += 32) {
+    for (int p = lane; p < np; p += 32) {
         const float2 xi = x2[p];
         float2 y[NC];
 #pragma unroll
@@ -163,10 +163,10 @@ __device__ __forceinline__ void pair_bin_tile(float2 (&acc)[NR][CAP], const floa
 
 template <int NR, int LM, int CAP, int B>
 __device__ __forceinline__ void pair_dispatch(int warp, float2 (&acc)[NR][CAP], const float* H,
-                                              const float* xs, int lane) {
+                                              const float* xs, int lane, int np) {
     if constexpr (B < PairConst<LM, CAP>::nbins) {
-        if (warp == B) pair_bin_tile<NR, LM, CAP, B>(acc, H, xs, lane);
-        else pair_dispatch<NR, LM, CAP, B + 1>(warp, acc, H, xs, lane);
+        if (warp == B) pair_bin_tile<NR, LM, CAP, B>(acc, H, xs, lane, np);
+        else pair_dispatch<NR, LM, CAP, B + 1>(warp, acc, H, xs, lane, np);
     }
 }
 
@@ -230,10 +230,20 @@ scf_coeff_pairs_kernel(ScfPairParams p) {
             if (idx < kPerWarp) accd[warp * kPerWarp + idx] += (double)mine[r];
         }
     };
-    auto load = [&](int tile) -> float4 {
-        const int64_t gi = (int64_t)tile * kPairTile + tid;
-        return (tid < kPairTile && tile < p.ntiles && gi < p.N) ? p.posm[gi]
-                                                              : make_float4(0.f, 0.f, 0.f, 0.f);
+    // this block's particles: one contiguous range, so that every block has
+    // the same work up to one particle pair (the last tile may be partial;
+    // its phase 2 runs over the pairs it holds)
+    const int64_t lo = (int64_t)blockIdx.x * p.per;
+    const int64_t hi = lo + p.per < p.N ? lo + p.per : p.N;
+    const int ntb = hi > lo ? (int)((hi - lo + kPairTile - 1) / kPairTile) : 0;
+    auto load = [&](int t) -> float4 {
+        const int64_t gi = lo + (int64_t)t * kPairTile + tid;
+        return (tid < kPairTile && t < ntb && gi < hi) ? p.posm[gi]
+                                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    auto pairs_in = [&](int t) {
+        const int64_t left = hi - lo - (int64_t)t * kPairTile;
+        return (int)(((left < kPairTile ? left : kPairTile) + 1) / 2);
     };
     auto phase1 = [&](const float4& v, float* Hs, float* Xs) {
         if (tid >= kPairTile) return;
@@ -248,18 +258,17 @@ scf_coeff_pairs_kernel(ScfPairParams p) {
         pair_angular<0, LM>(C, S, x * inv, y * inv, z * inv, -m * t, r * t * t, Hs, tid);
     };
 
-    float4 cur = load(blockIdx.x);
-    if (blockIdx.x < p.ntiles) phase1(cur, Hb(0), Xb(0));
-    cur = load(blockIdx.x + gridDim.x);
+    float4 cur = load(0);
+    if (ntb > 0) phase1(cur, Hb(0), Xb(0));
+    cur = load(1);
     __syncthreads();
     int since = 0, b = 0;
-    for (int tile = blockIdx.x; tile < p.ntiles; tile += gridDim.x, b ^= 1) {
-        const int nxt = tile + gridDim.x;
-        if (nxt < p.ntiles) {
+    for (int t = 0; t < ntb; ++t, b ^= 1) {
+        if (t + 1 < ntb) {
             phase1(cur, Hb(b ^ 1), Xb(b ^ 1));
-            cur = load(nxt + gridDim.x);
+            cur = load(t + 2);
         }
-        pair_dispatch<NR, LM, CAP, 0>(warp, acc, Hb(b), Xb(b), lane);
+        pair_dispatch<NR, LM, CAP, 0>(warp, acc, Hb(b), Xb(b), lane, pairs_in(t));
         if (++since == kPairFlushTiles) { flush(); since = 0; }
         __syncthreads();
     }
@@ -269,13 +278,17 @@ scf_coeff_pairs_kernel(ScfPairParams p) {
     for (int e = tid; e < NOUT; e += TH) out[e] = accd[e];
 }
 
-// block sums added in block order; one warp per output c[n][l*l+l+m]
+// Block sums added in block order; one warp per output c[n][l*l+l+m], four
+// warps per block so that the FP64 additions (slow on this GPU) are spread
+// over as many SMs as there are blocks.
+constexpr int kFinThreads = 128;
 template <int NR, int LM, int CAP>
-__global__ void scf_finalize_pairs_kernel(const double* __restrict__ partial, int nblocks,
-                                          double* __restrict__ coeffs) {
+__global__ void __launch_bounds__(kFinThreads)
+scf_finalize_pairs_kernel(const double* __restrict__ partial, int nblocks,
+                          double* __restrict__ coeffs) {
     constexpr int NJ = (LM + 1) * (LM + 1);
     constexpr int NOUT = PairConst<LM, CAP>::nbins * NR * CAP;
-    pdl_wait();
+    pdl_wait();   // the partials come from the coefficient kernel
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= NR * NJ) return;
@@ -287,7 +300,8 @@ __global__ void scf_finalize_pairs_kernel(const double* __restrict__ partial, in
     const int idx = (c_pair_plan<LM, CAP>.bin_of[col] * NR + n) * CAP +
                     c_pair_plan<LM, CAP>.slot_of[col];
     double s = 0.0;
-    for (int k = lane; k < nblocks; k += 32) s += partial[(size_t)k * NOUT + idx];
+#pragma unroll 4
+    for (int k = lane; k < nblocks; k += 32) s += __ldcg(partial + (size_t)k * NOUT + idx);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) {
@@ -311,7 +325,12 @@ inline int scf_coeffs_pairs_launch(const void* posm, int64_t N, double* coeffs, 
     const int ntiles = (int)((N + kPairTile - 1) / kPairTile);
     int grid = ctx.num_sms;
     if (grid > ntiles) grid = ntiles > 0 ? ntiles : 1;
-    ScfPairParams p{reinterpret_cast<const float4*>(posm), N, ntiles,
+    // contiguous, equal ranges (an even number of particles each): at
+    // N = 2^20 each of the 152 blocks takes 6900 particles (13 full tiles and
+    // one of 244) instead of 13 or 14 full tiles
+    int64_t per = (N + grid - 1) / grid;
+    per += per & 1;
+    ScfPairParams p{reinterpret_cast<const float4*>(posm), N, per,
                     reinterpret_cast<double*>(ws), ctx.err};
     int nblocks = 0;
     if (ntiles > 0) {
@@ -334,8 +353,9 @@ inline int scf_coeffs_pairs_launch(const void* posm, int64_t N, double* coeffs, 
     }
     stage_event(ctx, 1);
     const int nc = NR * (LM + 1) * (LM + 1);
-    if (launch_pdl(scf_finalize_pairs_kernel<NR, LM, CAP>, dim3((nc * 32 + 255) / 256), dim3(256),
-                   0, ctx.stream, (const double*)p.partial, nblocks, coeffs))
+    if (launch_pdl(scf_finalize_pairs_kernel<NR, LM, CAP>,
+                   dim3((nc * 32 + kFinThreads - 1) / kFinThreads), dim3(kFinThreads), 0,
+                   ctx.stream, (const double*)p.partial, nblocks, coeffs))
         return ETICS_ERR_CUDA;
     ++*ctx.launches;
     return ETICS_OK;
