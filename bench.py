@@ -1031,7 +1031,7 @@ def run_gemm(args):
     idx = torch.randint(0, M, (64,), generator=g, device=dev)
     ref = x[idx].float() @ w + net.params[K * N:].view(1, N)
     err = float(((y[idx] - ref).abs().max() / ref.abs().max()).item())
-    return {"experiment": "gemm", "kernel": "tc::gemm_kernel (tcgen05.mma kind::f16, TMEM accumulator)",
+    return {"experiment": "gemm", "kernel": "tc::gemm_tma_kernel (TMA operand ring, 128-byte swizzle, tcgen05.mma kind::f16, TMEM accumulator)",
             "M": M, "N": N, "K": K, "product_ms": ms, "epilogue_ms": statistics.median(epi_ms),
             "achieved_tflops": tf, "peak_tflops": peaks["bf16_tflops"],
             "frac": tf / peaks["bf16_tflops"], "peak_source": f"bf16_tflops of MEASURED_PEAKS.json ({src})",

@@ -700,6 +700,44 @@ int grid_1d(int64_t n, const LaunchCtx& ctx) {
     return (int)(g < 1 ? 1 : (g > cap ? cap : g));
 }
 
+// The driver's tensor-map encoder, fetched once through the runtime (the
+// library links only the CUDA runtime); null when the driver has none.
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+    static const EncodeTiledFn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return (EncodeTiledFn) nullptr;
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+// Tensor map of one bf16 operand for gemm_tma_kernel: R rows (M or N) by K,
+// X[r * ld + k] (k contiguous, MN == false) or X[k * ld + r] (r contiguous);
+// 128-byte swizzle, out-of-range elements read as zero.  False when the
+// layout does not meet TMA's rules (16-byte aligned base and row stride).
+bool operand_map(CUtensorMap* map, const bf16* X, int64_t ld, int R, int K, bool MN) {
+    const EncodeTiledFn enc = encode_tiled();
+    if (!enc || (reinterpret_cast<uintptr_t>(X) & 15) || ld <= 0 || (ld * 2) % 16 ||
+        ld >= (int64_t(1) << 31))
+        return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)(MN ? R : K), (cuuint64_t)(MN ? K : R)};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {64u, MN ? 64u : 128u};
+    const cuuint32_t estr[2] = {1u, 1u};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(X), dims, strides, box,
+               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
 // product + epilogue
 template <bool TA, bool TB>
 int gemm(const bf16* A, int64_t lda, const bf16* Bm, int64_t ldb, int M, int N, int K, float* part,
@@ -707,7 +745,16 @@ int gemm(const bf16* A, int64_t lda, const bf16* Bm, int64_t ldb, int M, int N, 
          const LaunchCtx& ctx) {
     const GemmShape s = gemm_shape(M, N, K);
     stage_event(ctx, 0);
-    if (s.tc) {
+    CUtensorMap ma, mb;
+    if (s.tc && operand_map(&ma, A, lda, M, K, TA) && operand_map(&mb, Bm, ldb, N, K, TB)) {
+        auto k = tc::gemm_tma_kernel<TA, TB>;
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tc::kSmemTmaBytes))
+            return ETICS_ERR_CUDA;
+        dim3 grid((N + tc::kN - 1) / tc::kN, (M + tc::kM - 1) / tc::kM, s.splits);
+        k<<<grid, tc::kThreads, tc::kSmemTmaBytes, ctx.stream>>>(ma, mb, part, M, N, K, s.kslice,
+                                                                 ctx.err);
+    } else if (s.tc) {
         auto k = tc::gemm_kernel<TA, TB>;
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)tc::kSmemBytes))

@@ -8,9 +8,14 @@
 // part[z][M][N] = sum over k in slice z of A(m, k) B(k, n), with
 //   A(m, k) = TA ? A[k * lda + m] : A[m * lda + k]
 //   B(k, n) = TB ? B[k * ldb + n] : B[n * ldb + k]
-// Block tile 128 x 128, K step 64 (four m128 n128 k16 MMAs), two stages.
+// Block tile 128 x 128, K step 64 (four m128 n128 k16 MMAs).  Two kernels:
+// gemm_tma_kernel, whose operand tiles arrive by TMA (cp.async.bulk.tensor)
+// with the 128-byte swizzle into a ring of stages, for operands whose
+// addresses and row strides are multiples of 16 bytes; and gemm_kernel, which
+// stages any layout with plain loads into the unswizzled canonical layout.
 #pragma once
 
+#include <cuda.h>   // CUtensorMap (the type only; the encoder is fetched at run time)
 #include <cuda_bf16.h>
 
 #include "etics_common.cuh"
@@ -114,6 +119,14 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
                  : "memory");
 }
 
+__device__ __forceinline__ void mma_id(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accum) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
 __device__ __forceinline__ void mma(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t accum) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -252,6 +265,196 @@ gemm_kernel(const bf16* __restrict__ A, int64_t lda, const bf16* __restrict__ B,
     bool drained = issued == 0 || mbar_wait(last_bar, last_par);
     if (!drained) drained = mbar_wait(last_bar, last_par, kDrainLimit);
     ok = __syncthreads_and(ok && drained && issued == nk);
+    if (!ok && tid == 0) report(err, ETICS_ERR_TIMEOUT);
+    tc_fence_after();
+    if (ok) {
+        // warp w reads TMEM lanes 32w..32w+31 = tile rows 32w.., 32 columns at a time
+        const int row = m0 + warp * 32 + lane;
+        float* out = part + (size_t)blockIdx.z * M * N;
+#pragma unroll 1
+        for (int c0 = 0; c0 < kN; c0 += 32) {
+            float v[32];
+            if (nk > 0) {
+                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) v[i] = 0.0f;
+            }
+            if (row < M) {
+                float* dst = out + (size_t)row * N + n0 + c0;
+#pragma unroll
+                for (int i = 0; i < 32; ++i)
+                    if (n0 + c0 + i < N) dst[i] = v[i];
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+}
+
+// ---------------------------------------------------------------------------
+// TMA-fed variant.  One lane of warp 0 copies the operand tiles of each K
+// step into a ring of kTmaStages stages (cp.async.bulk.tensor, 128-byte
+// swizzle), one lane of warp 1 issues the MMAs, the four warps read the
+// accumulator back.  Per stage s: full[s] completes when both tiles have
+// landed (one arrive with the expected byte count, then the copies' bytes),
+// empty[s] when the MMAs that read the stage have completed (tcgen05.commit).
+// Shared-memory layouts (bf16; each tile 1024-byte aligned):
+//   K-major operand (row r, k contiguous in memory): one box of 64 k x 128
+//     rows; row r at r * 128 bytes, its 16-byte chunks XOR-swizzled by r % 8;
+//     8-row groups 1024 bytes apart (the descriptor's stride byte offset);
+//     the next k16 step starts 32 bytes further.
+//   MN-major operand (k rows, r contiguous in memory): two boxes of 64 r x
+//     64 k, the second (r + 64) 8192 bytes after the first (leading byte
+//     offset); k-row at k * 128 bytes inside a box, 8-k groups 1024 bytes
+//     apart (stride byte offset); the next k16 step starts 2048 bytes further.
+// Every copy starts at an x coordinate that is a multiple of 64 elements
+// (128 bytes); boxes reaching past the tensor are zero-filled by the copy.
+// ---------------------------------------------------------------------------
+constexpr int kTmaStages = 4;
+constexpr uint32_t kTileBytes = (uint32_t)kTileElems * 2;   // 16 KB
+struct SmemTma {
+    bf16 a[kTmaStages][kTileElems];
+    bf16 b[kTmaStages][kTileElems];
+    unsigned long long full[kTmaStages];
+    unsigned long long empty[kTmaStages];
+    unsigned long long done;
+    uint32_t tmem;
+    int loaded;     // K steps whose copies were issued
+    int consumed;   // K steps whose MMAs were issued
+};
+constexpr size_t kSmemTmaBytes = sizeof(SmemTma) + 1024;
+static_assert(kTileBytes % 1024 == 0, "tiles keep the 1024-byte alignment of the swizzle");
+
+// shared-memory descriptor with the 128-byte swizzle (mode 2 in bits 61-63)
+__device__ __forceinline__ uint64_t make_desc_sw128(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// the (128 rows x 64 k) tile of one operand at (r0, k0) into dst
+template <bool MN>
+__device__ __forceinline__ void tma_tile(uint32_t dst, const CUtensorMap* map, int r0, int k0,
+                                         uint32_t bar) {
+    if (MN) {
+        tma_load_2d(dst, map, r0, k0, bar);
+        tma_load_2d(dst + 8192, map, r0 + 64, k0, bar);
+    } else {
+        tma_load_2d(dst, map, k0, r0, bar);
+    }
+}
+
+// descriptor of the k16 step kk of a tile at addr
+template <bool MN>
+__device__ __forceinline__ uint64_t tile_desc(uint32_t addr, int kk) {
+    return MN ? make_desc_sw128(addr + (uint32_t)kk * 2048u, 8192u, 1024u)
+              : make_desc_sw128(addr + (uint32_t)kk * 32u, 16u, 1024u);
+}
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(kThreads)
+gemm_tma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                float* __restrict__ part, int M, int N, int K, int kslice, unsigned* err) {
+    extern __shared__ unsigned char smem_raw[];
+    SmemTma& sm = *reinterpret_cast<SmemTma*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                              ~uintptr_t(1023));
+    constexpr uint32_t idesc = kIdesc | (TA ? 1u << 15 : 0u) | (TB ? 1u << 16 : 0u);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * kM, n0 = blockIdx.x * kN;
+    const int kb = blockIdx.z * kslice;
+    const int ke = min(K, kb + kslice);
+    const int nk = ke > kb ? (ke - kb + kK - 1) / kK : 0;
+
+    if (warp == 0) tmem_alloc(smem_u32(&sm.tmem), kTmemCols);
+    if (tid == 0) {
+        for (int s = 0; s < kTmaStages; ++s) {
+            mbar_init(smem_u32(&sm.full[s]), 1);
+            mbar_init(smem_u32(&sm.empty[s]), 1);
+        }
+        mbar_init(smem_u32(&sm.done), 1);
+        sm.loaded = 0;
+        sm.consumed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sm.tmem;
+
+    bool ok = true;
+    if (warp == 0 && lane == 0) {
+        // copies: stage s is refilled once the MMAs of its previous use are done
+        int kt = 0;
+        for (; kt < nk; ++kt) {
+            const int s = kt % kTmaStages;
+            if (kt >= kTmaStages &&
+                !mbar_wait(smem_u32(&sm.empty[s]), (uint32_t)((kt / kTmaStages - 1) & 1))) {
+                ok = false;
+                break;
+            }
+            const uint32_t full = smem_u32(&sm.full[s]);
+            mbar_expect_tx(full, 2 * kTileBytes);
+            const int k0 = kb + kt * kK;
+            tma_tile<TA>(smem_u32(sm.a[s]), &tmA, m0, k0, full);
+            tma_tile<TB>(smem_u32(sm.b[s]), &tmB, n0, k0, full);
+        }
+        sm.loaded = kt;
+    } else if (warp == 1 && lane == 0) {
+        // MMAs: four k16 steps per stage, then the stage is released
+        int kt = 0;
+        for (; kt < nk; ++kt) {
+            const int s = kt % kTmaStages;
+            if (!mbar_wait(smem_u32(&sm.full[s]), (uint32_t)((kt / kTmaStages) & 1))) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(sm.a[s]), b0 = smem_u32(sm.b[s]);
+#pragma unroll
+            for (int kk = 0; kk < kK / 16; ++kk)
+                mma_id(tmem, tile_desc<TA>(a0, kk), tile_desc<TB>(b0, kk), idesc,
+                       (kt > 0 || kk > 0) ? 1u : 0u);
+            commit(smem_u32(&sm.empty[s]));
+        }
+        sm.consumed = kt;
+        // arrives once every MMA issued above has completed
+        commit(smem_u32(&sm.done));
+    }
+    __syncwarp();
+    ok = __syncthreads_and(ok);
+    // Every MMA issued has completed when `done` completes; on a timed-out
+    // wait this is also the (bounded) wait before TMEM is freed, tried once
+    // more with a much longer bound, and copies still in flight are waited
+    // for (bounded) so that none lands after the block has exited.
+    bool drained = mbar_wait(smem_u32(&sm.done), 0u);
+    if (!drained) drained = mbar_wait(smem_u32(&sm.done), 0u, kDrainLimit);
+    if (!ok && tid == 0) {
+        for (int kt = sm.consumed; kt < sm.loaded; ++kt)
+            if (!mbar_wait(smem_u32(&sm.full[kt % kTmaStages]),
+                           (uint32_t)((kt / kTmaStages) & 1)))
+                drained = false;
+    }
+    ok = __syncthreads_and(ok && drained && sm.consumed == nk);
     if (!ok && tid == 0) report(err, ETICS_ERR_TIMEOUT);
     tc_fence_after();
     if (ok) {
