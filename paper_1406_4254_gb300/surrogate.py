@@ -6,7 +6,7 @@ coefficient pass (the first SCF pass, Sec. 3.3) runs only every
 ``stride``-th step and the steps between use a forecast of the coefficients
 from the last eight recomputed vectors: a cubic base, per-coefficient linear
 predictors fitted to a training trajectory, and a small MLP trained on what
-those miss.  Plain SCF remains the fallback and the judge: on every
+those miss.  Plain SCF remains the fallback and the check: on every
 recompute step the forecast that step would have used is compared with the
 recomputed coefficients through the relative acceleration error on a
 particle sample, and a forecast that misses the force-error budget switches
